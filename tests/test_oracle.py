@@ -1,0 +1,71 @@
+"""The CPU oracle against values fixed by the paper's definitions and by
+mathematics (hand-computed fixtures, enumeration of every cut, closed forms,
+Dinic, Hopcroft-Karp, the Koenig certificate)."""
+import numpy as np
+import pytest
+
+from tests import oracle_pins as P
+
+
+def test_golden_fixtures(oracle_mod):
+    P.pin_golden()
+
+
+def test_verifier_rejects_broken_flows(oracle_mod):
+    P.pin_verifier()
+
+
+def test_residual_distances(oracle_mod):
+    P.pin_residual_dist()
+
+
+def test_closed_forms(oracle_mod):
+    P.pin_closed_forms()
+
+
+def test_bruteforce_cuts(oracle_mod):
+    P.pin_bruteforce(count=1500)
+
+
+def test_matching_vs_hopcroft_karp(oracle_mod):
+    P.pin_matching()
+
+
+def test_dinic_agreement_medium(oracle_mod):
+    import workloads as W
+    for seed in range(12):
+        n = 50 + 37 * seed
+        inst = W.random_small(n, 6 * n, 100 + seed, cap_lo=0, cap_hi=50 + seed)
+        src, dst, cap = inst.numpy()
+        args = (n, src, dst, cap, inst.s, inst.t)
+        pr = oracle_mod.maxflow_pr(*args)
+        di = oracle_mod.maxflow_dinic(*args, want_flow=True)
+        assert pr["value"] == di["value"]
+        code, cut, side = oracle_mod.verify_flow(*args, pr["flow"], pr["value"])
+        assert code == 0 and cut == pr["value"]
+        # Both maximum flows give the same canonical cut side.
+        code2, _, side2 = oracle_mod.verify_flow(*args, di["flow"], di["value"])
+        assert code2 == 0 and (side == side2).all()
+        assert (side == pr["source_side"]).all()
+
+
+def test_grid_c1_value_is_stable(oracle_mod):
+    """The 64x64 grid with U[1,100] capacities, seed 1 (value written by
+    tests/golden/make_golden.py from the oracle, cross-checked by Dinic)."""
+    import json, os
+    import workloads as W
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_values.json")))
+    g = W.grid(64, 64, 1)
+    src, dst, cap = g.numpy()
+    v = oracle_mod.maxflow_pr(g.n, src, dst, cap, g.s, g.t)["value"]
+    assert v == gold["grid64x64_seed1"]
+    assert oracle_mod.maxflow_dinic(g.n, src, dst, cap, g.s, g.t)["value"] == v
+
+
+def test_invalid_inputs(oracle_mod):
+    with pytest.raises(RuntimeError):
+        oracle_mod.maxflow_pr(3, [0], [1], [1], 0, 0)         # s == t
+    with pytest.raises(RuntimeError):
+        oracle_mod.maxflow_pr(3, [0], [5], [1], 0, 1)         # id out of range
+    with pytest.raises(RuntimeError):
+        oracle_mod.maxflow_pr(3, [0], [1], [-1], 0, 1)        # negative capacity
