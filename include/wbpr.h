@@ -1,0 +1,246 @@
+/*
+ * wbpr.h -- C ABI of the GB300 workload-balanced push-relabel (WBPR) library.
+ *
+ * The library computes a maximum s-t flow and a minimum s-t cut of a directed
+ * graph with integer capacities (the problem of paper §2.1) on one CUDA GPU.
+ * The method is the lock-free push-relabel algorithm of Alg. 1 run in the
+ * vertex-centric, two-level-parallel form of Alg. 2 (§3.3) over the paper's
+ * compressed residual layouts RCSR and BCSR (§3.2, Fig. 2), with the global
+ * relabel heuristic of §2.2 and the gap heuristic.
+ *
+ * Conventions for every call:
+ *  - Vertices are 0 .. n-1.  Arcs are three int32 arrays src[m], dst[m],
+ *    cap[m] with cap >= 0.  Self-loops are accepted and carry flow 0.  Parallel
+ *    and antiparallel arcs are accepted.
+ *  - Integer arithmetic throughout: residual capacities int32, excesses and
+ *    flow values int64.  Results are exact.
+ *  - A stream argument is a cudaStream_t (NULL = the legacy default stream).
+ *    A handle must be used by one stream at a time; different handles are
+ *    independent.
+ *  - No call aborts, traps or prints.  Failures return a negative
+ *    wbpr_status (or NULL from the build calls); wbpr_last_error() and
+ *    wbpr_last_error_message() then describe the last failure of the calling
+ *    thread.
+ */
+#ifndef WBPR_H
+#define WBPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *wbpr_stream_t; /* same type as cudaStream_t */
+typedef struct wbpr_graph wbpr_graph;      /* opaque; owns all device memory of one instance */
+
+/* Residual-graph layouts of §3.2 (Fig. 2(c), 2(d)). */
+typedef enum {
+    WBPR_RCSR = 0, /* out-arc CSR plus an in-arc CSR whose entries hold flow_idx,
+                      the slot of the backward flow (constant-time backward access) */
+    WBPR_BCSR = 1  /* one merged neighbour list per vertex sorted by neighbour id;
+                      backward slot by binary search or a precomputed reverse index */
+} wbpr_layout;
+
+typedef enum {
+    WBPR_OK = 0,
+    WBPR_EINVAL = -1,    /* bad argument: n < 2, m < 0, s == t, id out of range,
+                            negative capacity, bad layout, NULL required pointer */
+    WBPR_ENOMEM = -2,    /* a device or host allocation failed */
+    WBPR_ECUDA = -3,     /* a CUDA runtime call failed (no device, launch error...) */
+    WBPR_ETIMEOUT = -4,  /* the iteration cap or a device wait limit was reached;
+                            the handle stays usable (solve again or destroy) */
+    WBPR_EOVERFLOW = -5, /* a vertex's capacity sum exceeds INT64_MAX, a merged
+                            pair c(u,v)+c(v,u) exceeds INT32_MAX, n >= 2^30, or the
+                            residual graph has 2^32 or more slots */
+    WBPR_ESTATE = -6     /* misuse: e.g. a batch entry is NULL or repeated */
+} wbpr_status;
+
+/* Tuning knobs.  None of them changes a result; all of them change speed. */
+typedef struct wbpr_options {
+    int32_t use_rev;          /* BCSR backward-slot lookup: 1 = reverse index (default),
+                                 0 = binary search in the neighbour's row (§3.2) */
+    int32_t gap;              /* 1 = gap heuristic on (default), 0 = off */
+    int32_t cycle;            /* push-relabel iterations between global relabels
+                                 (the "cycle" of Alg. 1); 0 = automatic */
+    int32_t small_max_degree; /* rows up to this length get a tile of
+                                 `small_tile` lanes (default 8) */
+    int32_t small_tile;       /* 4, 8 or 16 lanes (default 8) */
+    int32_t warp_max_degree;  /* longer rows (up to this) get one warp; longer
+                                 still get a whole thread block (default 2048) */
+    int32_t grid_blocks;      /* persistent grid size; 0 = automatic.  Clamped to
+                                 the number of co-resident blocks. */
+    int32_t barrier_timeout_ms; /* device wait limit (default 20000) */
+    int64_t max_iterations;   /* cap on push-relabel iterations per solve
+                                 (default 2^40); reaching it gives WBPR_ETIMEOUT */
+} wbpr_options;
+
+/* Counters of the last solve on a handle. */
+typedef struct wbpr_stats {
+    int64_t iterations;        /* push-relabel iterations (Alg. 2 passes), both phases */
+    int64_t phase1_iterations;
+    int64_t global_relabels;   /* backward BFS passes, both phases */
+    int64_t active_total;      /* sum over iterations of |AVQ| */
+    int64_t arcs_scanned;      /* residual-list entries read by the min-height scans */
+    int64_t gr_arcs_scanned;   /* entries read by the global-relabel BFS */
+    int64_t pushes;
+    int64_t relabels;
+    int64_t gaps;              /* gap-heuristic liftings applied */
+    int64_t written_off;       /* excess written off by global relabels (§2.2) */
+    double  solve_ms;          /* device time of the last wbpr_maxflow/_mincut solve */
+} wbpr_stats;
+
+/* Sizes of a built handle. */
+typedef struct wbpr_info {
+    int64_t n, m;              /* as given to wbpr_build */
+    int32_t s, t;
+    int32_t layout;            /* wbpr_layout */
+    int64_t slots;             /* BCSR: merged neighbour entries (2 x unordered pairs);
+                                  RCSR: out-arcs (= in-arcs) without self-loops */
+    int64_t max_degree;        /* longest residual list */
+    int64_t device_bytes;      /* device memory held by the handle */
+    int32_t grid_blocks;       /* persistent grid used by the solver */
+    int32_t num_sms;
+} wbpr_info;
+
+/*
+ * wbpr_build -- build the residual graph of §3.2 in the chosen layout.
+ *   n, m        vertex and arc counts (n >= 2, m >= 0, n < 2^30, m < 2^31).
+ *   src,dst,cap arc arrays of m int32 each; host or device pointers (detected
+ *               per pointer).  Read during the call only; the caller keeps them.
+ *   s, t        source and sink (0 <= s, t < n, s != t).
+ *   layout      WBPR_RCSR or WBPR_BCSR.
+ * Runs on the legacy default stream and returns after the graph is built.
+ * Returns a handle owning all device memory of the instance, or NULL on error
+ * (see wbpr_last_error()).
+ */
+wbpr_graph *wbpr_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                       const int32_t *cap, int32_t s, int32_t t, wbpr_layout layout);
+
+/* Same as wbpr_build, on `stream`, with options (NULL = defaults). */
+wbpr_graph *wbpr_build_ex(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                          const int32_t *cap, int32_t s, int32_t t, wbpr_layout layout,
+                          const wbpr_options *opts, wbpr_stream_t stream);
+
+/*
+ * wbpr_maxflow -- solve for a maximum flow (Alg. 1 driven by Alg. 2).
+ *   value      host pointer, required: receives the maximum flow value e(t).
+ *   edge_flow  NULL, or m int32 (host or device pointer): receives the flow on
+ *              every input arc in input order.  When non-NULL a second phase
+ *              returns stranded excess to s so the flow is valid: 0 <= f <= cap,
+ *              conservation at every vertex other than s and t.  Parallel arcs
+ *              share their pair's flow greedily in input order; a self-loop
+ *              gets 0.
+ * Re-solves from scratch on every call (idempotent).  Synchronises `stream`
+ * before returning.
+ */
+wbpr_status wbpr_maxflow(wbpr_graph *g, wbpr_stream_t stream, int64_t *value,
+                         int32_t *edge_flow);
+
+/*
+ * wbpr_maxflow_async -- as wbpr_maxflow but stream-ordered with no host
+ * synchronisation and no allocation: d_value (device int64, required) and
+ * d_edge_flow (device int32[m] or NULL) are written in stream order.  The
+ * status of the solve is read later by wbpr_solve_status().  The handle's
+ * own buffers are reused, so overlapping calls on one handle race.
+ */
+wbpr_status wbpr_maxflow_async(wbpr_graph *g, wbpr_stream_t stream, int64_t *d_value,
+                               int32_t *d_edge_flow);
+
+/* Device-side status of the last stream-ordered solve (synchronises `stream`). */
+wbpr_status wbpr_solve_status(wbpr_graph *g, wbpr_stream_t stream);
+
+/*
+ * wbpr_mincut -- a minimum s-t cut (max-flow = min-cut, §1).
+ *   cut_value   host pointer, required: the cut capacity (= the max-flow value).
+ *   source_side NULL, or n bytes (host or device pointer): 1 for the vertices
+ *               reachable from s in the residual graph of a maximum flow (the
+ *               smallest minimum-cut source side; the same for every maximum
+ *               flow), else 0.
+ * Reuses the state of a previous wbpr_maxflow with edge flows on this handle;
+ * otherwise solves first.  Synchronises `stream`.
+ */
+wbpr_status wbpr_mincut(wbpr_graph *g, wbpr_stream_t stream, int64_t *cut_value,
+                        uint8_t *source_side);
+
+/*
+ * wbpr_maxflow_batch -- solve `count` independent instances in one launch.
+ *   gs          count distinct handles (all built on this device).
+ *   values      host int64[count], required.
+ *   edge_flows  NULL, or count pointers each NULL or an int32[m_i] device
+ *               buffer for instance i.
+ * Each result equals that of wbpr_maxflow on the same handle.
+ */
+wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream_t stream,
+                               int64_t *values, int32_t *const *edge_flows);
+
+/* Release every device buffer of the handle.  NULL is accepted. */
+void wbpr_destroy(wbpr_graph *g);
+
+/* Options: defaults, read, replace (takes effect at the next solve). */
+void wbpr_default_options(wbpr_options *opts);
+wbpr_status wbpr_get_options(const wbpr_graph *g, wbpr_options *opts);
+wbpr_status wbpr_set_options(wbpr_graph *g, const wbpr_options *opts);
+
+/* Counters of the last solve; sizes of the handle. */
+wbpr_status wbpr_get_stats(const wbpr_graph *g, wbpr_stats *stats);
+wbpr_status wbpr_get_info(const wbpr_graph *g, wbpr_info *info);
+
+/* Last failure of the calling thread; a static description of a status. */
+wbpr_status wbpr_last_error(void);
+const char *wbpr_last_error_message(void);
+const char *wbpr_error_string(wbpr_status status);
+
+/*
+ * Device allocator hook.  By default the library allocates with
+ * cudaMallocAsync/cudaFreeAsync on the call's stream.  A host framework can
+ * route every device allocation of later calls through its own allocator
+ * (for example PyTorch's caching allocator).  alloc returns NULL on failure.
+ * Pass NULL functions to restore the default.  Not thread-safe against
+ * concurrent library calls.
+ */
+typedef void *(*wbpr_alloc_fn)(size_t bytes, wbpr_stream_t stream, void *ctx);
+typedef void (*wbpr_free_fn)(void *ptr, size_t bytes, wbpr_stream_t stream, void *ctx);
+wbpr_status wbpr_set_allocator(wbpr_alloc_fn alloc, wbpr_free_fn free_fn, void *ctx);
+
+/*
+ * Stage-level access for testing each step of the method on its own.
+ *   wbpr_run_stage(g, stream, stage, arg):
+ *     WBPR_STAGE_PREFLOW          reset to the initial residual graph, then the
+ *                                 preflow of Alg. 1 step 0 (h(s)=n, others 0)
+ *     WBPR_STAGE_GLOBAL_RELABEL   one global relabel of §2.2 on the current
+ *                                 state (backward BFS from t, write-off)
+ *     WBPR_STAGE_ITERATIONS       `arg` push-relabel iterations of Alg. 2 on
+ *                                 the current state, without global relabel
+ *   wbpr_export(g, what, host_dst, count): copy `count` elements of an
+ *     internal array to host memory (synchronous).
+ */
+enum {
+    WBPR_STAGE_PREFLOW = 1,
+    WBPR_STAGE_GLOBAL_RELABEL = 2,
+    WBPR_STAGE_ITERATIONS = 3
+};
+enum {
+    WBPR_ARRAY_HEIGHT = 1,      /* int32[n] */
+    WBPR_ARRAY_EXCESS = 2,      /* int64[n] */
+    WBPR_ARRAY_OFFSETS = 3,     /* int64[n+1]: BCSR rows / RCSR out rows */
+    WBPR_ARRAY_COL = 4,         /* int32[slots]: neighbour of each slot */
+    WBPR_ARRAY_CF = 5,          /* int32[slots]: residual capacity of each slot
+                                   (RCSR: of the forward arc) */
+    WBPR_ARRAY_CAP = 6,         /* int32[slots]: initial residual capacity */
+    WBPR_ARRAY_REV = 7,         /* uint32[slots]: BCSR reverse slot */
+    WBPR_ARRAY_BF = 8,          /* int32[slots]: RCSR backward residual (flow) */
+    WBPR_ARRAY_IN_OFFSETS = 9,  /* int64[n+1]: RCSR in rows */
+    WBPR_ARRAY_IN_COL = 10,     /* int32[slots]: RCSR in-arc tail */
+    WBPR_ARRAY_FLOW_IDX = 11,   /* uint32[slots]: RCSR in-arc -> out slot */
+    WBPR_ARRAY_ARC2SLOT = 12,   /* uint32[m]: input arc -> slot (UINT32_MAX for loops) */
+    WBPR_ARRAY_EXCESS_TOTAL = 13 /* int64[1] */
+};
+wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg);
+wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WBPR_H */

@@ -1,0 +1,477 @@
+// Graph builder: input arcs (COO, device) -> the residual layouts of §3.2.
+//
+// BCSR (Fig. 2(d)): every non-loop arc (u,v,c) contributes a half-entry
+// (row u, col v, c) and (row v, col u, 0).  Sorting the half-entries by
+// (row, col) and merging equal keys gives one slot per neighbour pair with
+// cf0 = sum of the capacities u -> v; rows come out sorted by neighbour id,
+// which the binary-search backward lookup of §3.2 needs.  rev[a] is the
+// slot of the paired entry, found once by that binary search.
+// RCSR (Fig. 2(c)): out rows = arcs sorted by (src, dst); in rows = the same
+// arcs sorted by (dst, src), each in entry keeping flow_idx, the out slot.
+// Sorting and scans use CUB (device radix sort / scan, header-only).
+#include <cub/cub.cuh>
+
+#include <stdint.h>
+
+#include <string>
+
+#include "handle.h"
+
+namespace wbpr {
+namespace {
+
+typedef unsigned long long u64;
+
+__global__ void validate_keys(long long m, int n, const int *src, const int *dst, const int *cap,
+                              u64 *key, unsigned *val, int *bad, unsigned long long *nonloop)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned long long local = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        int u = src[i], v = dst[i], c = cap[i];
+        if (u < 0 || u >= n || v < 0 || v >= n || c < 0) {
+            atomicOr(bad, 1);
+            u = v = 0;
+        }
+        if (u != v) {
+            key[i] = ((u64)(unsigned)u << 32) | (unsigned)v;
+            ++local;
+        } else {
+            key[i] = (u64)(unsigned)n << 32;  // self-loops sort after every real arc
+        }
+        val[i] = (unsigned)i;
+    }
+    if (local) atomicAdd(nonloop, local);
+}
+
+__global__ void gather_caps(long long mp, const unsigned *val, const int *cap, int *out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride)
+        out[j] = cap[val[j]];
+}
+
+__global__ void scatter_prefix(long long mp, const unsigned *val, const int *pre_sorted, int *prefix)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride)
+        prefix[val[j]] = pre_sorted[j];
+}
+
+__global__ void half_entries(long long mp, const u64 *key_sorted, const int *cap_sorted, u64 *key2,
+                             int *val2)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride) {
+        u64 k = key_sorted[j];
+        u64 rk = (k << 32) | (k >> 32);
+        key2[2 * j] = k;
+        val2[2 * j] = cap_sorted[j];
+        key2[2 * j + 1] = rk;
+        val2[2 * j + 1] = 0;
+    }
+}
+
+__global__ void run_heads(long long len, const u64 *key, unsigned *head)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride)
+        head[j] = (j == 0 || key[j] != key[j - 1]) ? 1u : 0u;
+}
+
+// slot_of = inclusive scan of run heads (1-based slot numbers).
+__global__ void merge_runs(long long len, const u64 *key, const int *val, const unsigned *slot_of,
+                           u64 *ukey, int *col, long long *csum)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
+        unsigned a = slot_of[j] - 1;
+        u64 k = key[j];
+        if (j == 0 || k != key[j - 1]) {
+            ukey[a] = k;
+            col[a] = (int)(k & 0xffffffffu);
+        }
+        int c = val[j];
+        if (c) atomicAdd((u64 *)(csum + a), (u64)(long long)c);
+    }
+}
+
+__global__ void narrow_caps(long long S, const long long *csum, int *cf0, int *cf, int *bad)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride) {
+        long long c = csum[a];
+        if (c > 0x7fffffffLL) {
+            atomicOr(bad, 2);
+            c = 0;
+        }
+        cf0[a] = (int)c;
+        cf[a] = (int)c;
+    }
+}
+
+// Row offsets from sorted row keys: off[v] = first slot with row >= v.
+__global__ void row_offsets(long long S, int n, const u64 *key, int shift, long long *off)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride) {
+        long long r = (long long)(key[a] >> shift);
+        long long rp = a == 0 ? -1 : (long long)(key[a - 1] >> shift);
+        for (long long v = rp + 1; v <= r; ++v) off[v] = a;
+        if (a == S - 1)
+            for (long long v = r + 1; v <= n; ++v) off[v] = S;
+    }
+}
+
+__global__ void fill_i64(long long len, long long *p, long long x)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += stride) p[i] = x;
+}
+
+__device__ __forceinline__ long long lower_bound_col(const int *col, long long b, long long e, int key)
+{
+    while (b < e) {
+        long long mid = (b + e) >> 1;
+        if (col[mid] < key) b = mid + 1;
+        else e = mid;
+    }
+    return b;
+}
+
+__global__ void reverse_slots(long long S, const u64 *ukey, const int *col, const long long *off,
+                              const int *cf0, unsigned *rev, int *bad)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride) {
+        int u = (int)(ukey[a] >> 32);
+        int v = col[a];
+        long long r = lower_bound_col(col, off[v], off[v + 1], u);
+        rev[a] = (unsigned)r;
+        if ((long long)cf0[a] + (long long)cf0[r] > 0x7fffffffLL) atomicOr(bad, 4);
+    }
+}
+
+__global__ void max_degree_kernel(int n, const long long *off, const long long *in_off,
+                                  unsigned long long *out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned long long mx = 0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += stride) {
+        long long d = off[v + 1] - off[v];
+        if (in_off) d += in_off[v + 1] - in_off[v];
+        if ((unsigned long long)d > mx) mx = (unsigned long long)d;
+    }
+    atomicMax(out, mx);
+}
+
+__global__ void arc_slots_bcsr(long long m, const int *src, const int *dst, const int *col,
+                               const long long *off, unsigned *arc2slot)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        int u = src[i], v = dst[i];
+        arc2slot[i] = (u == v) ? 0xffffffffu : (unsigned)lower_bound_col(col, off[u], off[u + 1], v);
+    }
+}
+
+__global__ void rcsr_out(long long mp, const unsigned *val, const int *dst, const int *cap,
+                         const u64 *key_sorted, int *col, int *cf0, int *cf, unsigned *arc2slot,
+                         u64 *key_in, unsigned *val_in)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride) {
+        unsigned i = val[j];
+        col[j] = dst[i];
+        cf0[j] = cap[i];
+        cf[j] = cap[i];
+        arc2slot[i] = (unsigned)j;
+        u64 k = key_sorted[j];
+        key_in[j] = (k << 32) | (k >> 32);
+        val_in[j] = (unsigned)j;
+    }
+}
+
+__global__ void rcsr_in(long long mp, const u64 *key_in_sorted, const unsigned *val_in_sorted,
+                        int *in_col, unsigned *flow_idx)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < mp; k += stride) {
+        in_col[k] = (int)(key_in_sorted[k] & 0xffffffffu);
+        flow_idx[k] = val_in_sorted[k];
+    }
+}
+
+inline int grid_for(long long work)
+{
+    long long b = (work + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+inline int bitlen(long long x)
+{
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+// Scratch allocations released at the end of the build.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<std::pair<void *, size_t>> held;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    void *get(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        void *p = dev_alloc(bytes, st);
+        if (p) held.push_back({p, bytes});
+        return p;
+    }
+    void release(void *p)
+    {
+        for (size_t i = 0; i < held.size(); ++i)
+            if (held[i].first == p) {
+                dev_free(p, held[i].second, st);
+                held.erase(held.begin() + (long)i);
+                return;
+            }
+    }
+    ~Scratch()
+    {
+        for (auto &b : held) dev_free(b.first, b.second, st);
+    }
+};
+
+#define BUILD_CUDA(call)                                                               \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return set_error(WBPR_ECUDA, std::string("build: ") + #call + ": " +       \
+                                             cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define BUILD_ALLOC(ptr, type, count, pool)                                            \
+    do {                                                                               \
+        ptr = (type *)(pool).get(sizeof(type) * (size_t)(count));                      \
+        if (!ptr) return set_error(WBPR_ENOMEM, "build: device allocation failed");    \
+    } while (0)
+
+#define OWN_ALLOC(ptr, type, count)                                                    \
+    do {                                                                               \
+        ptr = (type *)g->alloc(sizeof(type) * (size_t)(count), st);                    \
+        if (!ptr) return set_error(WBPR_ENOMEM, "build: device allocation failed");    \
+    } while (0)
+
+}  // namespace
+
+wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int *cap,
+                        cudaStream_t st)
+{
+    const long long n = g->n, m = g->m;
+    Scratch pool(st);
+    // ---- validate and form (src, dst) keys ---------------------------------
+    u64 *key1, *key1b;
+    unsigned *val1, *val1b;
+    int *bad;
+    unsigned long long *counter;
+    BUILD_ALLOC(key1, u64, m, pool);
+    BUILD_ALLOC(key1b, u64, m, pool);
+    BUILD_ALLOC(val1, unsigned, m, pool);
+    BUILD_ALLOC(val1b, unsigned, m, pool);
+    BUILD_ALLOC(bad, int, 4, pool);
+    BUILD_ALLOC(counter, unsigned long long, 4, pool);
+    BUILD_CUDA(cudaMemsetAsync(bad, 0, 4 * sizeof(int), st));
+    BUILD_CUDA(cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned long long), st));
+    if (m > 0) {
+        validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, src, dst, cap, key1, val1, bad, counter);
+        BUILD_CUDA(cudaGetLastError());
+    }
+    int h_bad = 0;
+    unsigned long long h_nonloop = 0;
+    BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaMemcpyAsync(&h_nonloop, counter, sizeof(h_nonloop), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaStreamSynchronize(st));
+    if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
+    const long long mp = (long long)h_nonloop;
+    g->mprime = mp;
+    const int end_bit = 32 + bitlen(n);
+
+    // ---- sort arcs by (src, dst); CUB radix sort is stable ---------------------
+    size_t temp_bytes = 0, need = 0;
+    cub::DoubleBuffer<u64> dk(key1, key1b);
+    cub::DoubleBuffer<unsigned> dv(val1, val1b);
+    if (m > 0) {
+        BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, need, dk, dv, (int64_t)m, 0, end_bit, st));
+        temp_bytes = need;
+    }
+    void *temp = nullptr;
+    if (temp_bytes) {
+        temp = pool.get(temp_bytes);
+        if (!temp) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+        BUILD_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, dk, dv, (int64_t)m, 0, end_bit, st));
+    }
+    u64 *ks = dk.Current();
+    unsigned *vs = dv.Current();
+
+    OWN_ALLOC(g->arc2slot, unsigned, m);
+    OWN_ALLOC(g->off, long long, n + 1);
+    unsigned long long *h_maxdeg_dev = counter + 1;
+
+    if (g->layout == WBPR_BCSR) {
+        // ---- duplicate prefix (edge-flow split in input order) ------------------
+        OWN_ALLOC(g->prefix, int, m);
+        OWN_ALLOC(g->cap_in, int, m);
+        if (m > 0) BUILD_CUDA(cudaMemcpyAsync(g->cap_in, cap, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st));
+        BUILD_CUDA(cudaMemsetAsync(g->prefix, 0, sizeof(int) * (size_t)(m > 0 ? m : 1), st));
+        int *cap_sorted, *pre_sorted;
+        BUILD_ALLOC(cap_sorted, int, mp, pool);
+        BUILD_ALLOC(pre_sorted, int, mp, pool);
+        if (mp > 0) {
+            gather_caps<<<grid_for(mp), 256, 0, st>>>(mp, vs, cap, cap_sorted);
+            BUILD_CUDA(cudaGetLastError());
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, ks, cap_sorted, pre_sorted, (int64_t)mp,
+                                                          cuda::std::equal_to<>(), st));
+            void *t2 = pool.get(nb);
+            if (!t2) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, ks, cap_sorted, pre_sorted, (int64_t)mp,
+                                                          cuda::std::equal_to<>(), st));
+            pool.release(t2);
+            scatter_prefix<<<grid_for(mp), 256, 0, st>>>(mp, vs, pre_sorted, g->prefix);
+            BUILD_CUDA(cudaGetLastError());
+        }
+        pool.release(pre_sorted);
+        // ---- half entries, sorted and merged ------------------------------------
+        const long long len = 2 * mp;
+        u64 *k2, *k2b;
+        int *v2, *v2b;
+        BUILD_ALLOC(k2, u64, len, pool);
+        BUILD_ALLOC(k2b, u64, len, pool);
+        BUILD_ALLOC(v2, int, len, pool);
+        BUILD_ALLOC(v2b, int, len, pool);
+        if (mp > 0) {
+            half_entries<<<grid_for(mp), 256, 0, st>>>(mp, ks, cap_sorted, k2, v2);
+            BUILD_CUDA(cudaGetLastError());
+        }
+        pool.release(cap_sorted);
+        pool.release(temp);
+        temp = nullptr;
+        pool.release(key1);
+        pool.release(key1b);
+        pool.release(val1);
+        pool.release(val1b);
+        cub::DoubleBuffer<u64> dk2(k2, k2b);
+        cub::DoubleBuffer<int> dv2(v2, v2b);
+        if (len > 0) {
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk2, dv2, (int64_t)len, 0, end_bit, st));
+            void *t3 = pool.get(nb);
+            if (!t3) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t3, nb, dk2, dv2, (int64_t)len, 0, end_bit, st));
+            pool.release(t3);
+        }
+        u64 *k2s = dk2.Current();
+        int *v2s = dv2.Current();
+        unsigned *heads;
+        BUILD_ALLOC(heads, unsigned, len, pool);
+        unsigned S = 0;
+        if (len > 0) {
+            run_heads<<<grid_for(len), 256, 0, st>>>(len, k2s, heads);
+            BUILD_CUDA(cudaGetLastError());
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceScan::InclusiveSum(nullptr, nb, heads, heads, (int64_t)len, st));
+            void *t4 = pool.get(nb);
+            if (!t4) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceScan::InclusiveSum(t4, nb, heads, heads, (int64_t)len, st));
+            pool.release(t4);
+            BUILD_CUDA(cudaMemcpyAsync(&S, heads + (len - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            BUILD_CUDA(cudaStreamSynchronize(st));
+        }
+        g->slots = S;
+        u64 *ukey;
+        long long *csum;
+        BUILD_ALLOC(ukey, u64, S, pool);
+        BUILD_ALLOC(csum, long long, S, pool);
+        OWN_ALLOC(g->col, int, S);
+        OWN_ALLOC(g->cf, int, S);
+        OWN_ALLOC(g->cf0, int, S);
+        OWN_ALLOC(g->rev, unsigned, S);
+        if (S > 0) {
+            BUILD_CUDA(cudaMemsetAsync(csum, 0, sizeof(long long) * S, st));
+            merge_runs<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, heads, ukey, g->col, csum);
+            BUILD_CUDA(cudaGetLastError());
+            narrow_caps<<<grid_for(S), 256, 0, st>>>(S, csum, g->cf0, g->cf, bad);
+            BUILD_CUDA(cudaGetLastError());
+            row_offsets<<<grid_for(S), 256, 0, st>>>(S, (int)n, ukey, 32, g->off);
+            BUILD_CUDA(cudaGetLastError());
+            reverse_slots<<<grid_for(S), 256, 0, st>>>(S, ukey, g->col, g->off, g->cf0, g->rev, bad);
+            BUILD_CUDA(cudaGetLastError());
+        } else {
+            fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
+            BUILD_CUDA(cudaGetLastError());
+        }
+        if (m > 0) {
+            arc_slots_bcsr<<<grid_for(m), 256, 0, st>>>(m, src, dst, g->col, g->off, g->arc2slot);
+            BUILD_CUDA(cudaGetLastError());
+        }
+        max_degree_kernel<<<grid_for(n), 256, 0, st>>>((int)n, g->off, nullptr, h_maxdeg_dev);
+        BUILD_CUDA(cudaGetLastError());
+    } else {
+        // ---- RCSR -----------------------------------------------------------------
+        g->slots = mp;
+        OWN_ALLOC(g->col, int, mp);
+        OWN_ALLOC(g->cf, int, mp);
+        OWN_ALLOC(g->cf0, int, mp);
+        OWN_ALLOC(g->bf, int, mp);
+        OWN_ALLOC(g->in_off, long long, n + 1);
+        OWN_ALLOC(g->in_col, int, mp);
+        OWN_ALLOC(g->flow_idx, unsigned, mp);
+        BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
+        u64 *kin, *kinb;
+        unsigned *vin, *vinb;
+        BUILD_ALLOC(kin, u64, mp, pool);
+        BUILD_ALLOC(kinb, u64, mp, pool);
+        BUILD_ALLOC(vin, unsigned, mp, pool);
+        BUILD_ALLOC(vinb, unsigned, mp, pool);
+        if (mp > 0) {
+            rcsr_out<<<grid_for(mp), 256, 0, st>>>(mp, vs, dst, cap, ks, g->col, g->cf0, g->cf,
+                                                   g->arc2slot, kin, vin);
+            BUILD_CUDA(cudaGetLastError());
+            BUILD_CUDA(cudaMemsetAsync(g->bf, 0, sizeof(int) * (size_t)mp, st));
+            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, ks, 32, g->off);
+            BUILD_CUDA(cudaGetLastError());
+            cub::DoubleBuffer<u64> dki(kin, kinb);
+            cub::DoubleBuffer<unsigned> dvi(vin, vinb);
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
+            void *t5 = pool.get(nb);
+            if (!t5) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t5, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
+            pool.release(t5);
+            rcsr_in<<<grid_for(mp), 256, 0, st>>>(mp, dki.Current(), dvi.Current(), g->in_col, g->flow_idx);
+            BUILD_CUDA(cudaGetLastError());
+            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, dki.Current(), 32, g->in_off);
+            BUILD_CUDA(cudaGetLastError());
+        } else {
+            fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
+            fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->in_off, 0);
+            BUILD_CUDA(cudaGetLastError());
+        }
+        max_degree_kernel<<<grid_for(n), 256, 0, st>>>((int)n, g->off, g->in_off, h_maxdeg_dev);
+        BUILD_CUDA(cudaGetLastError());
+    }
+    unsigned long long h_maxdeg = 0;
+    BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaMemcpyAsync(&h_maxdeg, h_maxdeg_dev, sizeof(h_maxdeg), cudaMemcpyDeviceToHost, st));
+    BUILD_CUDA(cudaStreamSynchronize(st));
+    if (h_bad) return set_error(WBPR_EOVERFLOW, "build: a merged pair's capacity exceeds INT32_MAX");
+    g->max_degree = (int64_t)h_maxdeg;
+    return WBPR_OK;
+}
+
+}  // namespace wbpr

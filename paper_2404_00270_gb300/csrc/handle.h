@@ -1,0 +1,90 @@
+// Host-side handle of one graph instance (the opaque wbpr_graph of wbpr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "wbpr.h"
+#include "wbpr_internal.cuh"
+
+namespace wbpr {
+
+// Device allocation through the allocator hook (api.cu).  Returns null on failure.
+void *dev_alloc(size_t bytes, cudaStream_t stream);
+void dev_free(void *p, size_t bytes, cudaStream_t stream);
+
+// Records a failure for wbpr_last_error()/wbpr_last_error_message().
+wbpr_status set_error(wbpr_status st, const std::string &msg);
+
+}  // namespace wbpr
+
+struct wbpr_graph {
+    int64_t n = 0, m = 0;
+    int32_t s = 0, t = 0;
+    int32_t layout = 0;
+    int64_t slots = 0;        // BCSR merged entries / RCSR arcs without loops
+    int64_t mprime = 0;       // input arcs that are not self-loops
+    int64_t max_degree = 0;
+    int device = 0;
+    int num_sms = 0;
+    int grid_blocks = 0;      // persistent grid of the last solve
+    wbpr_options opts;
+    wbpr_stats stats;
+    bool solved_flow = false; // phase 2 done on the current state
+    bool solved_value = false;
+
+    // graph (device)
+    long long *off = nullptr;
+    int *col = nullptr;
+    int *cf = nullptr;
+    int *cf0 = nullptr;
+    unsigned *rev = nullptr;
+    int *bf = nullptr;
+    long long *in_off = nullptr;
+    int *in_col = nullptr;
+    unsigned *flow_idx = nullptr;
+    unsigned *arc2slot = nullptr;
+    int *prefix = nullptr;    // BCSR: capacity of earlier duplicates of each input arc
+    int *cap_in = nullptr;    // BCSR: input capacities (edge-flow split)
+    // solver state (device)
+    long long *e = nullptr;
+    int *h = nullptr;
+    unsigned char *dead = nullptr;
+    int *count = nullptr;
+    int *q[2][wbpr::kClasses] = {{nullptr}};
+    wbpr::Ctl *ctl = nullptr;
+    long long *bstats = nullptr;
+    int bstats_blocks = 0;
+    int *edge_tmp = nullptr;           // device staging of edge flows for host outputs
+    unsigned char *side_tmp = nullptr; // device staging of the cut side for host outputs
+    // host
+    long long *pinned = nullptr;       // small pinned staging buffer
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    struct Block {
+        void *p;
+        size_t bytes;
+    };
+    std::vector<Block> blocks;  // every device allocation owned by the handle
+    int64_t device_bytes = 0;
+
+    void *alloc(size_t bytes, cudaStream_t st)
+    {
+        if (bytes == 0) bytes = 16;
+        void *p = wbpr::dev_alloc(bytes, st);
+        if (p) {
+            blocks.push_back({p, bytes});
+            device_bytes += (int64_t)bytes;
+        }
+        return p;
+    }
+};
+
+namespace wbpr {
+// Graph builders (builder.cu).  The inputs are device pointers.
+wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int *cap,
+                        cudaStream_t stream);
+}  // namespace wbpr

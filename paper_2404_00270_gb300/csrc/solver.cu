@@ -1,0 +1,929 @@
+// Persistent push-relabel solver for sm_103a.
+//
+// One cooperative launch runs a whole solve: reset + preflow (Alg. 1 step 0),
+// the global relabel of §2.2 as a level-synchronous backward BFS from the
+// sink, and the push-relabel iterations of Alg. 2 until the termination test
+// of Alg. 1 (e(s) + e(t) >= Excess_total) holds on the device; optionally a
+// second phase that returns stranded excess to s, and a forward BFS for the
+// minimum cut.  Grid-wide synchronisation (the grid_sync() of Alg. 2) is a
+// counter barrier with a time limit: a wait that gives up records
+// WBPR_ETIMEOUT in the control block and every block leaves the kernel.
+//
+// One iteration of Alg. 2:
+//   1. AVQ compaction: every block scans a contiguous range of vertices,
+//      stages the active ones (e > 0, h below the height cap, not s or t) in
+//      shared memory per tile class, and appends them to global queues with
+//      one atomic per class per flush (the atomic_add of Alg. 2, aggregated).
+//   2. grid_sync.
+//   3. Two-level parallelism: each active vertex is owned by one tile whose
+//      width follows its residual-list length: `SW` lanes (small rows), a
+//      warp, or the whole block (hub rows, taken dynamically).  The tile
+//      scans the list coalesced, gathers neighbour heights of residual arcs,
+//      and reduces (height, slot) keys to the minimum with warp shuffles;
+//      the tile's lane 0 then pushes min(e(u), cf(u,v')) with atomics when
+//      h(u) > h(v'), else relabels h(u) = h(v') + 1 (Alg. 1, relaxed push
+//      condition of §2.2).
+//   4. grid_sync.
+// Only the owner of u ever lowers e(u) or a residual capacity out of u, so
+// the pushed amount is always positive and no value goes negative; stale
+// neighbour heights are tolerated as in the lock-free algorithm.
+//
+// Gap heuristic: a relabel moves u from height hu to hn and keeps per-height
+// counts of vertices below n (count[], rebuilt at every global relabel from
+// the BFS level sizes).  When count[hu] drops to zero the level is a gap
+// candidate; at the next AVQ compaction (a quiescent point) it is re-checked
+// and, if still empty, every vertex with hu < h < n is lifted to n.
+#include <stdint.h>
+
+#include "wbpr_internal.cuh"
+
+namespace wbpr {
+namespace {
+
+typedef unsigned long long u64;
+constexpr u64 kNoKey = ~0ULL;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ u64 ld_acquire(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ u64 global_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_err(const Ctl *c)
+{
+    return *(volatile const int *)&c->err;
+}
+
+__device__ __forceinline__ u64 make_key(int h, unsigned idx)
+{
+    return ((u64)(unsigned)h << 32) | idx;
+}
+
+__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+
+template <int W>
+__device__ __forceinline__ u64 tile_min(u64 x)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) x = umin64(x, __shfl_xor_sync(kFull, x, o));
+    return x;
+}
+
+struct Smem {
+    int qbuf[kClasses][kQueueCap];
+    unsigned qcnt[kClasses];
+    unsigned qbase[kClasses];
+    u64 red[kWarps];
+    long long red64[kWarps];
+    long long stats[kStatCount];
+    unsigned item;
+    int ok;
+};
+
+struct Ctx {
+    const Params &P;
+    Smem &sm;
+    u64 bar_target;  // meaningful in thread 0 only
+    int gen;         // queue generation (uniform across the grid)
+};
+
+// Grid-wide barrier with a time limit.  Returns false on any device error.
+__device__ bool grid_sync(Ctx &c, int where)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Ctl *ctl = c.P.st.ctl;
+        c.bar_target += gridDim.x;
+        __threadfence();
+        atomicAdd(&ctl->bar, 1ULL);
+        int ok = 1;
+        u64 t0 = 0;
+        unsigned spins = 0;
+        while (ld_acquire(&ctl->bar) < c.bar_target) {
+            if (ld_err(ctl) != 0) { ok = 0; break; }
+            ++spins;
+            if ((spins & 255u) == 0) {
+                u64 now = global_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > c.P.timeout_ns) {
+                    atomicCAS(&ctl->err, 0, (int)WBPR_ETIMEOUT);
+                    ctl->err_where = where;
+                    ok = 0;
+                    break;
+                }
+            }
+            if (spins > 32) __nanosleep(40);
+        }
+        __threadfence();
+        if (ld_err(ctl) != 0) ok = 0;
+        c.sm.ok = ok;
+    }
+    __syncthreads();
+    return c.sm.ok != 0;
+}
+
+template <int L>
+__device__ __forceinline__ long long degree(const GraphDev &g, int v)
+{
+    long long d = __ldg(g.off + v + 1) - __ldg(g.off + v);
+    if (L == kRCSR) d += __ldg(g.in_off + v + 1) - __ldg(g.in_off + v);
+    return d;
+}
+
+__device__ __forceinline__ int classify(const Params &P, long long d)
+{
+    return d <= P.small_max ? 0 : (d <= P.warp_max ? 1 : 2);
+}
+
+// ---------------------------------------------------------------------------
+// Queue production: stage in shared memory, flush with one atomic per class.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void q_append(Ctx &c, int slot3, int set, int cls, int v)
+{
+    unsigned pos = atomicAdd(&c.sm.qcnt[cls], 1u);
+    if (pos < (unsigned)kQueueCap) {
+        c.sm.qbuf[cls][pos] = v;
+    } else {
+        unsigned gpos = atomicAdd(&c.P.st.ctl->q_count[slot3][cls], 1u);
+        c.P.st.q[set][cls][gpos] = v;
+    }
+}
+
+// All threads of the block call this.
+__device__ void q_flush(Ctx &c, int slot3, int set)
+{
+    __syncthreads();
+    if (threadIdx.x < kClasses) {
+        unsigned k = c.sm.qcnt[threadIdx.x];
+        if (k > (unsigned)kQueueCap) k = kQueueCap;
+        c.sm.qbase[threadIdx.x] = k ? atomicAdd(&c.P.st.ctl->q_count[slot3][threadIdx.x], k) : 0u;
+        c.sm.qcnt[threadIdx.x] = k;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cls = 0; cls < kClasses; ++cls) {
+        unsigned k = c.sm.qcnt[cls];
+        int *dst = c.P.st.q[set][cls] + c.sm.qbase[cls];
+        for (unsigned i = threadIdx.x; i < k; i += kBlock) dst[i] = c.sm.qbuf[cls][i];
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses) c.sm.qcnt[threadIdx.x] = 0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctl *ctl = c.P.st.ctl;
+        int z = (gen + 2) % 3;
+        for (int k = 0; k < kClasses; ++k) ctl->q_count[z][k] = 0;
+        ctl->q_grab[z] = 0;
+        ctl->gap_level[z] = kUnvisited;
+    }
+}
+
+__device__ long long block_sum(Ctx &c, long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) c.sm.red64[threadIdx.x >> 5] = x;
+    __syncthreads();
+    long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) s += c.sm.red64[w];
+    return s;  // valid in thread 0
+}
+
+__device__ u64 block_min(Ctx &c, u64 x)
+{
+    x = tile_min<32>(x);
+    if ((threadIdx.x & 31) == 0) c.sm.red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        u64 y = threadIdx.x < kWarps ? c.sm.red[threadIdx.x] : kNoKey;
+        y = tile_min<32>(y);
+        if (threadIdx.x == 0) c.sm.red[0] = y;
+    }
+    __syncthreads();
+    u64 r = c.sm.red[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Residual-list scans.  `rounds_*` are uniform over the tile (or warp).
+// BCSR: entries [b, e) of u's merged row; key index = k - b.
+// RCSR: out entries first (index j - ob), then in entries (dout + k - ib).
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ u64 scan_bcsr(const GraphDev &g, const int *h, long long b,
+                                         long long e, int lane, int rounds)
+{
+    u64 best = kNoKey;
+#pragma unroll 4
+    for (int r = 0; r < rounds; ++r) {
+        long long k = b + (long long)r * W + lane;
+        if (k < e) {
+            int cfk = __ldcg(g.cf + k);
+            int v = __ldg(g.col + k);
+            if (cfk > 0) best = umin64(best, make_key(__ldcg(h + v), (unsigned)(k - b)));
+        }
+    }
+    return best;
+}
+
+template <int W>
+__device__ __forceinline__ u64 scan_rcsr(const GraphDev &g, const int *h, long long ob,
+                                         long long oe, long long ib, long long ie, int lane,
+                                         int rounds_out, int rounds_in)
+{
+    u64 best = kNoKey;
+#pragma unroll 4
+    for (int r = 0; r < rounds_out; ++r) {
+        long long j = ob + (long long)r * W + lane;
+        if (j < oe) {
+            int c = __ldcg(g.cf + j);
+            int v = __ldg(g.col + j);
+            if (c > 0) best = umin64(best, make_key(__ldcg(h + v), (unsigned)(j - ob)));
+        }
+    }
+    const unsigned dout = (unsigned)(oe - ob);
+#pragma unroll 4
+    for (int r = 0; r < rounds_in; ++r) {
+        long long k = ib + (long long)r * W + lane;
+        if (k < ie) {
+            unsigned j = __ldg(g.flow_idx + k);
+            int v = __ldg(g.in_col + k);
+            int c = __ldcg(g.bf + j);
+            if (c > 0) best = umin64(best, make_key(__ldcg(h + v), dout + (unsigned)(k - ib)));
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ long long lower_bound_col(const int *col, long long b, long long e,
+                                                     int key)
+{
+    while (b < e) {
+        long long mid = (b + e) >> 1;
+        if (__ldg(col + mid) < key) b = mid + 1;
+        else e = mid;
+    }
+    return b;
+}
+
+// Push or relabel for the owner of u (one thread).  Alg. 1: if h(u) > h'
+// push d = min(e(u), cf(u, v')) with four atomics, else h(u) = h' + 1.
+template <int L>
+__device__ void apply_op(Ctx &c, int u, u64 key, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    int *h = P.st.h;
+    long long *e = P.st.e;
+    const int hu = __ldcg(h + u);
+    if (key != kNoKey) {
+        const int hmin = (int)(key >> 32);
+        const unsigned idx = (unsigned)(key & 0xffffffffu);
+        if (hu > hmin) {
+            long long eu = __ldcg(e + u);
+            int v;
+            int *dec;
+            int *inc;
+            if (L == kBCSR) {
+                long long a = __ldg(g.off + u) + idx;
+                v = __ldg(g.col + a);
+                long long ra;
+                if (P.use_rev) {
+                    ra = __ldg(g.rev + a);
+                } else {
+                    ra = lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), u);
+                }
+                dec = g.cf + a;
+                inc = g.cf + ra;
+            } else {
+                long long ob = __ldg(g.off + u);
+                unsigned dout = (unsigned)(__ldg(g.off + u + 1) - ob);
+                if (idx < dout) {
+                    long long j = ob + idx;
+                    v = __ldg(g.col + j);
+                    dec = g.cf + j;
+                    inc = g.bf + j;
+                } else {
+                    long long k = __ldg(g.in_off + u) + (idx - dout);
+                    unsigned j = __ldg(g.flow_idx + k);
+                    v = __ldg(g.in_col + k);
+                    dec = g.bf + j;
+                    inc = g.cf + j;
+                }
+            }
+            int cav = __ldcg(dec);
+            long long d = eu < (long long)cav ? eu : (long long)cav;
+            if (d > 0) {
+                atomicSub(dec, (int)d);
+                atomicAdd((u64 *)(e + u), (u64)(-d));
+                atomicAdd(inc, (int)d);
+                atomicAdd((u64 *)(e + v), (u64)d);
+                atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], 1ull);
+            }
+            return;
+        }
+    }
+    int hn = (key == kNoKey) ? hcap : (int)(key >> 32) + 1;
+    if (hn > hcap) hn = hcap;
+    __stcg(h + u, hn);
+    atomicAdd((unsigned long long *)&c.sm.stats[kStatRelabels], 1ull);
+    if (phase1 && P.gap) {
+        int *count = P.st.count;
+        const int n = g.n;
+        if (hn < n) atomicAdd(count + hn, 1);
+        int prev = atomicSub(count + hu, 1);
+        if (prev == 1) atomicMin(&P.st.ctl->gap_level[c.gen % 3], hu);
+    }
+}
+
+// Tile of W <= 32 lanes (all 32 lanes of the warp call this; u < 0 = idle).
+template <int L, int W>
+__device__ void pr_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
+{
+    const GraphDev &g = c.P.g;
+    long long ob = 0, oe = 0, ib = 0, ie = 0;
+    int ro = 0, ri = 0;
+    if (u >= 0) {
+        ob = __ldg(g.off + u);
+        oe = __ldg(g.off + u + 1);
+        ro = (int)((oe - ob + W - 1) / W);
+        if (L == kRCSR) {
+            ib = __ldg(g.in_off + u);
+            ie = __ldg(g.in_off + u + 1);
+            ri = (int)((ie - ib + W - 1) / W);
+        }
+    }
+    ro = __reduce_max_sync(kFull, ro);
+    if (L == kRCSR) ri = __reduce_max_sync(kFull, ri);
+    u64 best = (L == kBCSR) ? scan_bcsr<W>(g, c.P.st.h, ob, oe, sl, ro)
+                            : scan_rcsr<W>(g, c.P.st.h, ob, oe, ib, ie, sl, ro, ri);
+    best = tile_min<W>(best);
+    if (u >= 0 && sl == 0) {
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)((oe - ob) + (ie - ib)));
+        apply_op<L>(c, u, best, phase1, hcap);
+    }
+}
+
+template <int L>
+__device__ void pr_block(Ctx &c, int u, bool phase1, int hcap)
+{
+    const GraphDev &g = c.P.g;
+    long long ob = __ldg(g.off + u), oe = __ldg(g.off + u + 1), ib = 0, ie = 0;
+    int ro = (int)((oe - ob + kBlock - 1) / kBlock), ri = 0;
+    if (L == kRCSR) {
+        ib = __ldg(g.in_off + u);
+        ie = __ldg(g.in_off + u + 1);
+        ri = (int)((ie - ib + kBlock - 1) / kBlock);
+    }
+    u64 best = (L == kBCSR)
+                   ? scan_bcsr<kBlock>(g, c.P.st.h, ob, oe, threadIdx.x, ro)
+                   : scan_rcsr<kBlock>(g, c.P.st.h, ob, oe, ib, ie, threadIdx.x, ro, ri);
+    best = block_min(c, best);
+    if (threadIdx.x == 0) {
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)((oe - ob) + (ie - ib)));
+        apply_op<L>(c, u, best, phase1, hcap);
+    }
+    __syncthreads();
+}
+
+// Consume the AVQ of generation `gen` (step 3 of an iteration).
+template <int L, int SW>
+__device__ void pr_process(Ctx &c, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    Ctl *ctl = P.st.ctl;
+    const int gen = c.gen, s3 = gen % 3, set = gen & 1;
+    reset_rotating(c, gen);
+    const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
+    const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
+    const unsigned c2 = __ldcg(&ctl->q_count[s3][2]);
+    // hub rows: one block each, taken dynamically
+    if (c2) {
+        const int *q2 = P.st.q[set][2];
+        for (;;) {
+            if (threadIdx.x == 0) c.sm.item = atomicAdd(&ctl->q_grab[s3], 1u);
+            __syncthreads();
+            unsigned i = c.sm.item;
+            __syncthreads();
+            if (i >= c2) break;
+            pr_block<L>(c, __ldcg(q2 + i), phase1, hcap);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const unsigned nwarps = gridDim.x * kWarps;
+    {
+        const int *q1 = P.st.q[set][1];
+        for (unsigned i = gwarp; i < c1; i += nwarps) pr_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
+    }
+    {
+        constexpr unsigned TPW = 32 / SW;
+        const unsigned gt0 = gwarp * TPW, ntiles = nwarps * TPW;
+        const int *q0 = P.st.q[set][0];
+        if (c0 > gt0) {
+            const unsigned rounds = (c0 - gt0 + ntiles - 1) / ntiles;
+            const unsigned sub = lane / SW, sl = lane % SW;
+            for (unsigned r = 0; r < rounds; ++r) {
+                unsigned i = gt0 + sub + r * ntiles;
+                int u = i < c0 ? __ldcg(q0 + i) : -1;
+                pr_tile<L, SW>(c, u, sl, phase1, hcap);
+            }
+        }
+    }
+}
+
+// Step 1 of an iteration: build the AVQ of generation `gen`.
+template <int L>
+__device__ void build_avq(Ctx &c, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int n = g.n, s = g.s, t = g.t;
+    const int gen = c.gen, s3 = gen % 3, set = gen & 1;
+    // Gap check at this quiescent point (phase 1 only).
+    int gap = kUnvisited;
+    if (phase1 && P.gap) {
+        int cand = __ldcg(&P.st.ctl->gap_level[(gen + 2) % 3]);
+        if (cand < n && __ldcg(P.st.count + cand) == 0) gap = cand;
+    }
+    const long long chunk = ((long long)n + gridDim.x - 1) / gridDim.x;
+    const long long v0 = chunk * blockIdx.x;
+    const long long v1 = v0 + chunk < n ? v0 + chunk : n;
+    long long nact = 0, lifted = 0;
+    for (long long base = v0; base < v1; base += kBlock) {
+        long long v = base + threadIdx.x;
+        if (v < v1) {
+            int hv = __ldcg(P.st.h + v);
+            if (gap != kUnvisited && hv > gap && hv < n && v != s) {
+                hv = n;
+                __stcg(P.st.h + v, n);
+                ++lifted;
+            }
+            if (v != s && v != t && hv < hcap) {
+                if (__ldcg(P.st.e + v) > 0) {
+                    q_append(c, s3, set, classify(P, degree<L>(g, (int)v)), (int)v);
+                    ++nact;
+                }
+            }
+        }
+        __syncthreads();
+        unsigned mx = c.sm.qcnt[0];
+        if (c.sm.qcnt[1] > mx) mx = c.sm.qcnt[1];
+        if (c.sm.qcnt[2] > mx) mx = c.sm.qcnt[2];
+        __syncthreads();  // every thread has read the counts before new appends
+        if (mx > (unsigned)(kQueueCap - kBlock)) q_flush(c, s3, set);
+    }
+    q_flush(c, s3, set);
+    if (nact) atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)nact);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && gap != kUnvisited)
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatGaps], 1ull);
+    (void)lifted;
+}
+
+// ---------------------------------------------------------------------------
+// Level-synchronous BFS (global relabel and cut).
+//   kBfsBackward: from `target`, visit v when the residual arc v -> w exists
+//                 (w = frontier vertex); h[v] = level value (CAS on kUnvisited)
+//   kBfsForward:  from s, visit v when the residual arc w -> v exists; marks in
+//                 count[] (CAS 0 -> 1)
+// ---------------------------------------------------------------------------
+enum { kBfsBackward = 0, kBfsForward = 1 };
+
+template <int L, int DIR>
+__device__ __forceinline__ bool residual_to(const Params &P, long long slot, bool in_slot,
+                                            int w)
+{
+    const GraphDev &g = P.g;
+    if (L == kBCSR) {
+        if (DIR == kBfsForward) return __ldcg(g.cf + slot) > 0;
+        long long ra;
+        if (P.use_rev) {
+            ra = __ldg(g.rev + slot);
+        } else {
+            int v = __ldg(g.col + slot);
+            ra = lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), w);
+        }
+        return __ldcg(g.cf + ra) > 0;
+    } else {
+        if (!in_slot) {  // out slot j of w: arc w -> v
+            return DIR == kBfsForward ? __ldcg(g.cf + slot) > 0 : __ldcg(g.bf + slot) > 0;
+        }
+        unsigned j = __ldg(g.flow_idx + slot);  // in slot of w: arc v -> w is out slot j
+        return DIR == kBfsForward ? __ldcg(g.bf + j) > 0 : __ldcg(g.cf + j) > 0;
+    }
+}
+
+template <int L, int DIR>
+__device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int n3)
+{
+    const Params &P = c.P;
+    if (DIR == kBfsBackward) {
+        int *h = P.st.h;
+        if (__ldcg(h + v) == kUnvisited && atomicCAS(h + v, kUnvisited, val) == kUnvisited)
+            q_append(c, n3, nset, classify(P, degree<L>(P.g, v)), v);
+    } else {
+        int *mark = P.st.count;
+        if (__ldcg(mark + v) == 0 && atomicCAS(mark + v, 0, 1) == 0)
+            q_append(c, n3, nset, classify(P, degree<L>(P.g, v)), v);
+    }
+}
+
+// Scan frontier vertex w with `W` lanes starting at lane `sl`.
+template <int L, int DIR, int W>
+__device__ void bfs_row(Ctx &c, int w, int sl, int val, int nset, int n3)
+{
+    const GraphDev &g = c.P.g;
+    long long ob = __ldg(g.off + w), oe = __ldg(g.off + w + 1);
+    for (long long k = ob + sl; k < oe; k += W) {
+        if (residual_to<L, DIR>(c.P, k, false, w)) bfs_visit<L, DIR>(c, __ldg(g.col + k), val, nset, n3);
+    }
+    if (L == kRCSR) {
+        long long ib = __ldg(g.in_off + w), ie = __ldg(g.in_off + w + 1);
+        for (long long k = ib + sl; k < ie; k += W) {
+            if (residual_to<L, DIR>(c.P, k, true, w)) bfs_visit<L, DIR>(c, __ldg(g.in_col + k), val, nset, n3);
+        }
+    }
+}
+
+// Consume frontier generation `gen`, produce generation gen + 1.
+template <int L, int DIR, int SW>
+__device__ void bfs_level(Ctx &c, int val)
+{
+    const Params &P = c.P;
+    Ctl *ctl = P.st.ctl;
+    const int gen = c.gen, s3 = gen % 3, set = gen & 1;
+    const int n3 = (gen + 1) % 3, nset = (gen + 1) & 1;
+    reset_rotating(c, gen);
+    const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
+    const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
+    const unsigned c2 = __ldcg(&ctl->q_count[s3][2]);
+    long long scanned = 0;
+    if (c2) {
+        const int *q2 = P.st.q[set][2];
+        for (;;) {
+            if (threadIdx.x == 0) c.sm.item = atomicAdd(&ctl->q_grab[s3], 1u);
+            __syncthreads();
+            unsigned i = c.sm.item;
+            __syncthreads();
+            if (i >= c2) break;
+            int w = __ldcg(q2 + i);
+            bfs_row<L, DIR, kBlock>(c, w, threadIdx.x, val, nset, n3);
+            if (threadIdx.x == 0) scanned += degree<L>(P.g, w);
+            __syncthreads();
+            unsigned mx = c.sm.qcnt[0];
+            if (c.sm.qcnt[1] > mx) mx = c.sm.qcnt[1];
+            if (c.sm.qcnt[2] > mx) mx = c.sm.qcnt[2];
+            if (mx > (unsigned)(kQueueCap / 2)) q_flush(c, n3, nset);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const unsigned nwarps = gridDim.x * kWarps;
+    {
+        const int *q1 = P.st.q[set][1];
+        for (unsigned i = gwarp; i < c1; i += nwarps) {
+            int w = __ldcg(q1 + i);
+            bfs_row<L, DIR, 32>(c, w, lane, val, nset, n3);
+            if (lane == 0) scanned += degree<L>(P.g, w);
+        }
+    }
+    {
+        const int *q0 = P.st.q[set][0];
+        const unsigned gt = (blockIdx.x * kBlock + threadIdx.x) / SW;
+        const unsigned ntiles = gridDim.x * kBlock / SW;
+        const int sl = threadIdx.x % SW;
+        for (unsigned i = gt; i < c0; i += ntiles) {
+            int w = __ldcg(q0 + i);
+            bfs_row<L, DIR, SW>(c, w, sl, val, nset, n3);
+            if (sl == 0) scanned += degree<L>(P.g, w);
+        }
+    }
+    q_flush(c, n3, nset);
+    if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
+}
+
+__device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v, int cls)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c.P.st.q[gen & 1][cls][0] = v;
+        c.P.st.ctl->q_count[gen % 3][cls] = 1;
+    }
+}
+
+// Global relabel (§2.2): heights = base + BFS distance to `target` over
+// residual arcs, never through `excluded`; unreachable vertices get
+// `unreach`.  Phase 1 writes off the excess of newly unreachable vertices
+// (Excess_total -= e(v), once per vertex) and rebuilds the gap counts.
+template <int L, int SW>
+__device__ bool global_relabel(Ctx &c, bool phase1)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int n = g.n;
+    const int target = phase1 ? g.t : g.s;
+    const int excluded = phase1 ? g.s : g.t;
+    const int base = phase1 ? 0 : n;
+    const int unreach = phase1 ? n : 2 * n;
+    const bool gap = phase1 && P.gap;
+    const long long stride = (long long)gridDim.x * kBlock;
+    for (long long v = blockIdx.x * kBlock + threadIdx.x; v <= n; v += stride) {
+        if (gap) __stcg(P.st.count + v, 0);
+        if (v == n || v == excluded) continue;
+        if (phase1 && P.st.dead[v]) continue;
+        __stcg(P.st.h + v, v == target ? base : kUnvisited);
+    }
+    seed_queue(c, c.gen, target, classify(P, degree<L>(g, target)));
+    if (!grid_sync(c, 10)) return false;
+    for (int level = 0;; ++level) {
+        const unsigned tot = __ldcg(&P.st.ctl->q_count[c.gen % 3][0]) +
+                             __ldcg(&P.st.ctl->q_count[c.gen % 3][1]) +
+                             __ldcg(&P.st.ctl->q_count[c.gen % 3][2]);
+        if (tot == 0) break;
+        if (gap && blockIdx.x == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
+        bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
+        if (!grid_sync(c, 11)) return false;
+        c.gen++;
+    }
+    long long wo = 0;
+    for (long long v = blockIdx.x * kBlock + threadIdx.x; v < n; v += stride) {
+        if (v == excluded) continue;
+        if (__ldcg(P.st.h + v) == kUnvisited) {
+            __stcg(P.st.h + v, unreach);
+            if (phase1 && !P.st.dead[v]) {
+                P.st.dead[v] = 1;
+                wo += __ldcg(P.st.e + v);
+            }
+        }
+    }
+    long long bw = block_sum(c, wo);
+    if (threadIdx.x == 0 && bw) {
+        atomicAdd((u64 *)&P.st.ctl->excess_total, (u64)(-bw));
+        atomicAdd((u64 *)&P.st.ctl->written_off, (u64)bw);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.st.ctl->global_relabels++;
+    return grid_sync(c, 12);
+}
+
+// `max_it` iterations of Alg. 2 (fewer if the AVQ empties).  Returns false
+// on a device error; *it_done receives the count.
+template <int L, int SW>
+__device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_total)
+{
+    const Params &P = c.P;
+    const int hcap = phase1 ? P.g.n : 2 * P.g.n;
+    for (long long i = 0; i < max_it; ++i) {
+        build_avq<L>(c, phase1, hcap);
+        if (!grid_sync(c, 20)) return false;
+        const int s3 = c.gen % 3;
+        const unsigned tot = __ldcg(&P.st.ctl->q_count[s3][0]) + __ldcg(&P.st.ctl->q_count[s3][1]) +
+                             __ldcg(&P.st.ctl->q_count[s3][2]);
+        if (tot == 0) {
+            reset_rotating(c, c.gen);
+            if (!grid_sync(c, 21)) return false;
+            c.gen++;
+            break;
+        }
+        pr_process<L, SW>(c, phase1, hcap);
+        if (!grid_sync(c, 22)) return false;
+        c.gen++;
+        ++*it_total;
+        if (*it_total >= P.max_iterations) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                atomicCAS(&P.st.ctl->err, 0, (int)WBPR_ETIMEOUT);
+                P.st.ctl->err_where = 23;
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+template <int L, int SW>
+__device__ bool run_phase(Ctx &c, bool phase1, long long *it_total)
+{
+    const Params &P = c.P;
+    Ctl *ctl = P.st.ctl;
+    if (!global_relabel<L, SW>(c, phase1)) return false;
+    int idle_rounds = 0;
+    for (;;) {
+        const long long es = __ldcg(P.st.e + P.g.s), et = __ldcg(P.st.e + P.g.t);
+        const long long goal = phase1 ? __ldcg(&ctl->excess_total) : __ldcg(&ctl->preflow_total);
+        if (es + et >= goal) break;
+        const long long before = *it_total;
+        if (!iterate<L, SW>(c, phase1, P.cycle, it_total)) return false;
+        // A global relabel right after an empty AVQ must settle the test above;
+        // two rounds in a row without any iteration mean it cannot: give up
+        // instead of looping.
+        idle_rounds = (*it_total == before) ? idle_rounds + 1 : 0;
+        if (idle_rounds >= 2) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                atomicCAS(&ctl->err, 0, (int)WBPR_ESTATE);
+                ctl->err_where = 24;
+            }
+            return false;
+        }
+        if (!global_relabel<L, SW>(c, phase1)) return false;
+    }
+    return true;
+}
+
+// Reset the residual graph and state, then the preflow of Alg. 1 step 0.
+template <int L>
+__device__ bool preflow(Ctx &c)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const long long stride = (long long)gridDim.x * kBlock;
+    const long long tid = blockIdx.x * kBlock + threadIdx.x;
+    for (long long k = tid; k < g.slots; k += stride) {
+        g.cf[k] = __ldg(g.cf0 + k);
+        if (L == kRCSR) g.bf[k] = 0;
+    }
+    for (long long v = tid; v < g.n; v += stride) {
+        P.st.e[v] = 0;
+        P.st.h[v] = (v == g.s) ? g.n : 0;
+        P.st.dead[v] = 0;
+    }
+    if (!grid_sync(c, 1)) return false;
+    const long long b = __ldg(g.off + g.s), e = __ldg(g.off + g.s + 1);
+    long long sum = 0;
+    for (long long k = b + tid; k < e; k += stride) {
+        int cap = g.cf[k];
+        if (cap <= 0) continue;
+        g.cf[k] = 0;
+        int v = __ldg(g.col + k);
+        if (L == kBCSR) {
+            long long ra = P.use_rev ? (long long)__ldg(g.rev + k)
+                                     : lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), g.s);
+            atomicAdd(g.cf + ra, cap);
+        } else {
+            atomicAdd(g.bf + k, cap);
+        }
+        atomicAdd((u64 *)(P.st.e + v), (u64)cap);
+        sum += cap;
+    }
+    long long bs = block_sum(c, sum);
+    if (threadIdx.x == 0 && bs) {
+        atomicAdd((u64 *)&P.st.ctl->excess_total, (u64)bs);
+        atomicAdd((u64 *)&P.st.ctl->preflow_total, (u64)bs);
+    }
+    return grid_sync(c, 2);
+}
+
+// Forward BFS from s over residual arcs; source_side and cut capacity.
+template <int L, int SW>
+__device__ bool min_cut(Ctx &c)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int n = g.n;
+    const long long stride = (long long)gridDim.x * kBlock;
+    const long long tid = blockIdx.x * kBlock + threadIdx.x;
+    int *mark = P.st.count;
+    for (long long v = tid; v <= n; v += stride) __stcg(mark + v, v == g.s ? 1 : 0);
+    seed_queue(c, c.gen, g.s, classify(P, degree<L>(g, g.s)));
+    if (!grid_sync(c, 30)) return false;
+    for (;;) {
+        const unsigned tot = __ldcg(&P.st.ctl->q_count[c.gen % 3][0]) +
+                             __ldcg(&P.st.ctl->q_count[c.gen % 3][1]) +
+                             __ldcg(&P.st.ctl->q_count[c.gen % 3][2]);
+        if (tot == 0) break;
+        bfs_level<L, kBfsForward, SW>(c, 1);
+        if (!grid_sync(c, 31)) return false;
+        c.gen++;
+    }
+    // cut capacity: arcs from the marked side to the rest (initial capacities)
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const long long nw = stride >> 5;
+    long long sum = 0;
+    for (long long u = gw; u < n; u += nw) {
+        if (!__ldcg(mark + u)) continue;
+        long long b = __ldg(g.off + u), e = __ldg(g.off + u + 1);
+        for (long long k = b + lane; k < e; k += 32)
+            if (!__ldcg(mark + __ldg(g.col + k))) sum += __ldg(g.cf0 + k);
+    }
+    long long bs = block_sum(c, sum);
+    if (threadIdx.x == 0 && bs) atomicAdd((u64 *)&P.st.ctl->cut_value, (u64)bs);
+    if (P.source_side)
+        for (long long v = tid; v < n; v += stride) P.source_side[v] = (unsigned char)(__ldcg(mark + v) != 0);
+    return grid_sync(c, 32);
+}
+
+template <int L, int SW>
+__global__ void __launch_bounds__(kBlock) solve_kernel(Params P)
+{
+    __shared__ Smem sm;
+    Ctx c{P, sm, 0ull, 0};
+    if (threadIdx.x < kClasses) sm.qcnt[threadIdx.x] = 0;
+    if (threadIdx.x < kStatCount) sm.stats[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) P.st.ctl->gap_level[k] = kUnvisited;
+    __syncthreads();
+    long long it_total = 0;
+    bool ok = true;
+    if (P.mode & kModePreflow) ok = preflow<L>(c);
+    if (ok && (P.mode & kModePhase1)) {
+        ok = run_phase<L, SW>(c, true, &it_total);
+        if (blockIdx.x == 0 && threadIdx.x == 0) P.st.ctl->phase1_iterations = it_total;
+    }
+    if (ok && (P.mode & kModeGrOnce)) ok = global_relabel<L, SW>(c, true);
+    if (ok && (P.mode & kModeIters)) ok = iterate<L, SW>(c, true, P.iters_arg, &it_total);
+    if (ok && (P.mode & kModePhase2)) ok = run_phase<L, SW>(c, false, &it_total);
+    if (ok && (P.mode & kModeCut)) ok = min_cut<L, SW>(c);
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.st.ctl->iterations = it_total;
+    __syncthreads();
+    if (threadIdx.x < kStatCount) P.st.bstats[(long long)blockIdx.x * kStatCount + threadIdx.x] = sm.stats[threadIdx.x];
+}
+
+// Edge flows in input order.  BCSR: the merged pair's net flow u -> v is
+// cf0(a) - cf(a); when positive it is split over the duplicate input arcs
+// u -> v greedily in input order (prefix = capacity of earlier duplicates).
+// RCSR: the flow of arc j is its backward residual bf(j).
+__global__ void edge_flow_kernel(int layout, long long m, const unsigned *arc2slot,
+                                 const int *cf0, const int *cf, const int *bf, const int *prefix,
+                                 const int *cap_in, int *edge_flow)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        unsigned a = arc2slot[i];
+        int f = 0;
+        if (a != 0xffffffffu) {
+            if (layout == kBCSR) {
+                long long net = (long long)cf0[a] - (long long)cf[a];
+                if (net > 0) {
+                    long long x = net - prefix[i];
+                    if (x < 0) x = 0;
+                    if (x > cap_in[i]) x = cap_in[i];
+                    f = (int)x;
+                }
+            } else {
+                f = bf[a];
+            }
+        }
+        edge_flow[i] = f;
+    }
+}
+
+}  // namespace
+
+template <int L, int SW>
+static void *kernel_ptr() { return (void *)solve_kernel<L, SW>; }
+
+static void *pick_kernel(int layout, int small_tile)
+{
+    if (layout == kBCSR) {
+        if (small_tile == 4) return kernel_ptr<kBCSR, 4>();
+        if (small_tile == 16) return kernel_ptr<kBCSR, 16>();
+        return kernel_ptr<kBCSR, 8>();
+    }
+    if (small_tile == 4) return kernel_ptr<kRCSR, 4>();
+    if (small_tile == 16) return kernel_ptr<kRCSR, 16>();
+    return kernel_ptr<kRCSR, 8>();
+}
+
+cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pick_kernel(layout, small_tile),
+                                                         kBlock, 0);
+}
+
+cudaError_t solver_launch(int layout, int small_tile, int grid, const Params &p,
+                          cudaStream_t stream)
+{
+    Params local = p;
+    void *args[] = {&local};
+    return cudaLaunchCooperativeKernel(pick_kernel(layout, small_tile), dim3(grid), dim3(kBlock),
+                                       args, 0, stream);
+}
+
+cudaError_t launch_edge_flow(int layout, long long m, const unsigned *arc2slot, const int *cf0,
+                             const int *cf, const int *bf, const int *prefix, const int *cap_in,
+                             int *edge_flow, cudaStream_t stream)
+{
+    if (m <= 0) return cudaSuccess;
+    long long blocks = (m + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    edge_flow_kernel<<<(int)blocks, 256, 0, stream>>>(layout, m, arc2slot, cf0, cf, bf, prefix,
+                                                      cap_in, edge_flow);
+    return cudaGetLastError();
+}
+
+}  // namespace wbpr

@@ -1,0 +1,122 @@
+// Internal types shared by the translation units of the WBPR library.
+//
+// Device data layout (one handle = one graph instance):
+//   BCSR (§3.2, Fig. 2(d)): off[n+1] (int64) rows of merged, id-sorted
+//     neighbour lists; per slot a: col[a] (int32 neighbour), cf[a] (int32
+//     residual capacity of the arc row(a) -> col[a]), cf0[a] (its initial
+//     value), rev[a] (uint32 slot of the paired entry in col[a]'s row).
+//   RCSR (§3.2, Fig. 2(c)): off[n+1] out rows, per out slot j: col[j] (head),
+//     cf[j] (forward residual), bf[j] (backward residual = flow on arc j),
+//     cf0[j] (capacity); in_off[n+1] in rows, per in slot k: in_col[k]
+//     (tail), flow_idx[k] (the out slot j of the same arc).
+//   Per vertex: e[n] (int64 excess), h[n] (int32 height), dead[n] (uint8:
+//     excess already written off), count[n+1] (int32 vertices per height,
+//     gap heuristic), six int32[n] queues (2 generations x 3 tile classes).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wbpr.h"
+
+namespace wbpr {
+
+constexpr int kBlock = 256;         // threads per block of the persistent solver
+constexpr int kWarps = kBlock / 32;
+constexpr int kClasses = 3;         // tile classes: small tile, warp, block
+constexpr int kQueueCap = 1024;     // per-class shared-memory staging of queue appends
+constexpr int kUnvisited = 0x7fffffff;
+
+enum Layout : int { kRCSR = 0, kBCSR = 1 };
+
+// Per-block statistics slots (reduced on the host after a launch).
+enum Stat : int {
+    kStatPushes = 0,
+    kStatRelabels,
+    kStatArcs,
+    kStatGrArcs,
+    kStatActive,
+    kStatGaps,
+    kStatCount
+};
+
+// Device control block, cleared before every solver launch.
+struct __align__(128) Ctl {
+    unsigned long long bar;  // grid barrier: total arrivals
+    unsigned long long pad0[15];
+    int err;                 // wbpr_status of a device-side failure (0 = none)
+    int err_where;           // which wait gave up
+    int gap_level[3];        // lowest emptied height level, by queue generation % 3
+    int pad1;
+    long long excess_total;  // Excess_total of Alg. 1
+    long long preflow_total; // excess created by the preflow
+    long long written_off;
+    long long iterations;
+    long long phase1_iterations;
+    long long global_relabels;
+    long long cut_value;
+    unsigned q_count[3][kClasses];  // queue sizes by generation % 3 and class
+    unsigned q_grab[3];             // dynamic work counter of the block class
+    int done;
+};
+
+struct GraphDev {
+    int n, s, t;
+    long long slots;
+    const long long *off;
+    const int *col;
+    int *cf;
+    const int *cf0;
+    const unsigned *rev;        // BCSR, may be null when use_rev = 0
+    int *bf;                    // RCSR
+    const long long *in_off;    // RCSR
+    const int *in_col;          // RCSR
+    const unsigned *flow_idx;   // RCSR
+};
+
+struct StateDev {
+    long long *e;
+    int *h;
+    unsigned char *dead;
+    int *count;
+    int *q[2][kClasses];
+    Ctl *ctl;
+    long long *bstats;          // [gridDim.x][kStatCount]
+};
+
+// Solver launch modes (bit mask).
+enum Mode : int {
+    kModePreflow = 1,       // reset residual graph and state, then preflow
+    kModePhase1 = 2,        // global relabel + iterations until e(s)+e(t) >= Excess_total
+    kModeGrOnce = 4,        // one global relabel (phase 1 semantics)
+    kModeIters = 8,         // `iters_arg` iterations, no global relabel
+    kModePhase2 = 16,       // return stranded excess to s
+    kModeCut = 32           // forward BFS from s: source side and cut capacity
+};
+
+struct Params {
+    GraphDev g;
+    StateDev st;
+    int mode;
+    long long iters_arg;
+    int cycle;
+    int gap;
+    int use_rev;
+    int small_max;
+    int warp_max;
+    long long max_iterations;
+    unsigned long long timeout_ns;
+    unsigned char *source_side;  // kModeCut output (device, n bytes) or null
+};
+
+// Launch helpers implemented in solver.cu.
+cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks);
+cudaError_t solver_launch(int layout, int small_tile, int grid, const Params &p,
+                          cudaStream_t stream);
+
+// Edge-flow kernels (solver.cu).
+cudaError_t launch_edge_flow(int layout, long long m, const unsigned *arc2slot,
+                             const int *cf0, const int *cf, const int *bf, const int *prefix,
+                             const int *cap_in, int *edge_flow, cudaStream_t stream);
+
+}  // namespace wbpr

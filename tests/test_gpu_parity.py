@@ -1,0 +1,233 @@
+"""CUDA path vs the oracle, through the C ABI.  Integer work: every compared
+quantity (flow value, cut capacity, canonical cut side, builder arrays,
+preflow state, global-relabel heights) must match bit for bit; edge flows
+are not unique and are checked by the optimality certificate."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from oracle import layouts
+from tests.golden import FIXTURES, load
+from tests.gpu_helpers import LAYOUTS, check_against_oracle, gpu_solve, layout_code, wb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("name", FIXTURES)
+def test_golden_fixtures(name, layout):
+    f = load(name)
+    got = check_against_oracle(f["n"], f["src"], f["dst"], f["cap"], f["s"], f["t"], layout)
+    assert got["value"] == f["value"]
+    assert np.array_equal(got["side"], f["source_side"])
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_random_small_vs_bruteforce(layout):
+    for seed in range(300):
+        n = 2 + seed % 14
+        m = (seed * 5) % 48
+        inst = W.random_small(n, m, 7000 + seed, cap_lo=0 if seed % 3 else 1, cap_hi=1 + seed % 23)
+        src, dst, cap = inst.numpy()
+        bv, bs = oracle.mincut_brute(n, src, dst, cap, inst.s, inst.t)
+        got = gpu_solve(n, src, dst, cap, inst.s, inst.t, layout)
+        assert got["value"] == bv == got["cut"], (seed, got["value"], bv)
+        assert np.array_equal(got["side"], bs), seed
+        code, _, _ = oracle.verify_flow(n, src, dst, cap, inst.s, inst.t, got["flow"], bv)
+        assert code == 0, (seed, code)
+
+
+def test_bcsr_binary_search_mode_matches():
+    m = wb()
+    o = m.wbpr_default_options()
+    o.use_rev = 0
+    for seed in range(40):
+        inst = W.random_small(30 + seed, 200, 9100 + seed, cap_lo=0, cap_hi=40)
+        src, dst, cap = inst.numpy()
+        check_against_oracle(inst.n, src, dst, cap, inst.s, inst.t, "bcsr", o)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_grid_64x64(layout):
+    g = W.grid(64, 64, 1)
+    src, dst, cap = g.numpy()
+    got = check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout)
+    assert got["value"] == 1971
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_grid_uniform_closed_form(layout):
+    g = W.grid(64, 64, 1, uniform_cap=50)
+    src, dst, cap = g.numpy()
+    got = gpu_solve(g.n, src, dst, cap, g.s, g.t, layout)
+    assert got["value"] == 64 * 50
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_medium_random_with_duplicates(layout):
+    for seed in range(6):
+        n = 500 + 300 * seed
+        inst = W.random_small(n, 8 * n, 500 + seed, cap_lo=0, cap_hi=100)
+        src, dst, cap = inst.numpy()
+        # duplicate a slice of arcs and reverse another slice (antiparallel pairs)
+        src = np.concatenate([src, src[:200], dst[200:400]])
+        dst = np.concatenate([dst, dst[:200], src[200:400]])
+        cap = np.concatenate([cap, cap[:200], cap[200:400]])
+        check_against_oracle(n, src, dst, cap, inst.s, inst.t, layout)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_rmat_14(layout):
+    g = W.rmat(14, 16, 2)
+    src, dst, cap = g.numpy()
+    got = check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout)
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_values.json")))
+    assert got["value"] == gold["rmat14_seed2"]
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_bipartite_matching(layout):
+    g = W.bipartite_zipf(1 << 12, 1 << 12, 3)
+    src, dst, cap = g.numpy()
+    got = check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout)
+    lr = g.meta["lr_edges"]
+    nl = g.meta["nl"]
+    hk = oracle.matching_hk(nl, g.meta["nr"], src[:lr], dst[:lr] - nl)
+    assert got["value"] == hk
+
+
+def test_option_sweep_same_results():
+    m = wb()
+    g = W.rmat(12, 16, 5)
+    src, dst, cap = g.numpy()
+    ref = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t)
+    for layout in LAYOUTS:
+        for tile, smax, wmax, gap, cycle, grid in [(4, 4, 64, 1, 1, 0), (16, 16, 16, 0, 1000, 0),
+                                                   (8, 0, 0, 1, 7, 3), (8, 8, 2048, 1, 64, 1)]:
+            o = m.wbpr_default_options()
+            o.small_tile, o.small_max_degree, o.warp_max_degree = tile, smax, wmax
+            o.gap, o.cycle, o.grid_blocks = gap, cycle, grid
+            check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o, ref=ref)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_builder_arrays_bit_exact(layout):
+    m = wb()
+    for seed in range(4):
+        inst = W.random_small(200 + 50 * seed, 3000, 300 + seed, cap_lo=0, cap_hi=1000)
+        src, dst, cap = inst.numpy()
+        src = np.concatenate([src, src[:100], dst[100:300], [5, 9]])
+        dst = np.concatenate([dst, dst[:100], src[100:300], [5, 9]])
+        cap = np.concatenate([cap, cap[:100], cap[100:300], [3, 4]])
+        G = m.wbpr_build(inst.n, src.size, src, dst, cap, inst.s, inst.t, layout_code(layout))
+        ref = layouts.bcsr(inst.n, src, dst, cap) if layout == "bcsr" else layouts.rcsr(inst.n, src, dst, cap)
+        for key, val in ref.items():
+            got = m.wbpr_export(G, key)
+            assert np.array_equal(got, val), (layout, key)
+        G.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_preflow_and_global_relabel_stages(layout):
+    """Preflow state and global-relabel heights (BFS distances to t over the
+    residual arcs of the exported snapshot, s excluded) bit-exact."""
+    m = wb()
+    g = W.rmat(11, 8, 9)
+    src, dst, cap = g.numpy()
+    n, s, t = g.n, g.s, g.t
+    G = m.wbpr_build(n, src.size, src, dst, cap, s, t, layout_code(layout))
+    m.wbpr_run_stage(G, 1)   # preflow
+    h = m.wbpr_export(G, "height")
+    e = m.wbpr_export(G, "excess")
+    exp_h = np.zeros(n, np.int32)
+    exp_h[s] = n
+    assert np.array_equal(h, exp_h)
+    exp_e = np.zeros(n, np.int64)
+    np.add.at(exp_e, dst[src == s], cap[src == s].astype(np.int64))
+    exp_e[s] = 0
+    loops = (src == s) & (dst == s)
+    assert not loops.any()
+    assert np.array_equal(e, exp_e)
+    assert m.wbpr_export(G, "excess_total")[0] == cap[src == s].sum()
+    for rounds in (0, 3, 25):
+        if rounds:
+            m.wbpr_run_stage(G, 3, rounds)   # push-relabel iterations, no relabel
+        m.wbpr_run_stage(G, 2)               # one global relabel
+        tail, head, res = _residual_arcs(m, G, n, layout)
+        dist = oracle.residual_dist(n, tail, head, res, t, s, 0, n, n)
+        h = m.wbpr_export(G, "height")
+        alive = dist < n
+        assert np.array_equal(h[alive], dist[alive]), rounds
+        assert (h[~alive] >= n).all()
+    G.close()
+
+
+def _residual_arcs(m, G, n, layout):
+    off = m.wbpr_export(G, "offsets")
+    col = m.wbpr_export(G, "col")
+    cf = m.wbpr_export(G, "cf").astype(np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int32), np.diff(off))
+    if layout == "bcsr":
+        return rows, col, cf
+    bf = m.wbpr_export(G, "bf").astype(np.int64)
+    # forward residual u -> v = cf, backward residual v -> u = bf
+    return np.concatenate([rows, col]), np.concatenate([col, rows]), np.concatenate([cf, bf])
+
+
+def test_resolve_is_idempotent():
+    m = wb()
+    g = W.grid(32, 32, 3)
+    src, dst, cap = g.numpy()
+    G = m.wbpr_build(g.n, g.m, src, dst, cap, g.s, g.t, m.WBPR_BCSR)
+    a = m.wbpr_maxflow(G)
+    b = m.wbpr_maxflow(G)
+    flow = np.zeros(g.m, np.int32)   # host buffer: copied back by the library
+    c = m.wbpr_maxflow(G, None, flow)
+    assert a == b == c
+    assert oracle.verify_flow(g.n, src, dst, cap, g.s, g.t, flow, c)[0] == 0
+    G.close()
+
+
+def test_iteration_cap_reports_timeout_and_handle_survives():
+    m = wb()
+    g = W.grid(32, 32, 4)
+    src, dst, cap = g.numpy()
+    o = m.wbpr_default_options()
+    o.max_iterations = 2
+    G = m.wbpr_build(g.n, g.m, src, dst, cap, g.s, g.t, m.WBPR_BCSR, o)
+    with pytest.raises(m.WbprError) as e:
+        m.wbpr_maxflow(G)
+    assert e.value.status == -4
+    o.max_iterations = 1 << 40
+    m.wbpr_set_options(G, o)
+    ref = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t)["value"]
+    assert m.wbpr_maxflow(G) == ref
+    G.close()
+
+
+def test_device_errors_are_reported():
+    m = wb()
+    with pytest.raises(m.WbprError) as e:
+        m.wbpr_build(10, 2, [0, 1], [1, 11], [1, 1], 0, 9)    # id out of range
+    assert e.value.status == -1
+    with pytest.raises(m.WbprError) as e:
+        m.wbpr_build(10, 1, [0], [1], [-1], 0, 9)              # negative capacity
+    assert e.value.status == -1
+    big = 2 ** 31 - 1
+    with pytest.raises(m.WbprError) as e:
+        m.wbpr_build(4, 2, [0, 1], [1, 0], [big, 5], 0, 3)     # pair sum overflows int32
+    assert e.value.status == -5
+
+
+def test_degenerate_graphs():
+    for layout in LAYOUTS:
+        # no arcs at all; only self-loops; s -> t directly
+        got = gpu_solve(2, [], [], [], 0, 1, layout)
+        assert got["value"] == 0 and got["side"].tolist() == [1, 0]
+        got = gpu_solve(3, [0, 1, 2], [0, 1, 2], [5, 5, 5], 0, 2, layout)
+        assert got["value"] == 0 and got["flow"].tolist() == [0, 0, 0]
+        got = gpu_solve(2, [0, 0, 1], [1, 1, 0], [5, 7, 3], 0, 1, layout)
+        assert got["value"] == 12 and got["flow"].tolist() == [5, 7, 0]

@@ -1,0 +1,79 @@
+"""Host-side checks that need no GPU: the C ABI library loads, exports every
+function that include/wbpr.h declares, and rejects bad arguments before any
+CUDA call; the layout restatements match hand-built examples."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def wb():
+    import paper_2404_00270_gb300 as wb
+    from paper_2404_00270_gb300 import _build
+    _build.build()
+    wb.load()
+    return wb
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "wbpr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wbpr_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree(wb):
+    assert _declared() == sorted(wb.EXPORTED_SYMBOLS)
+
+
+def test_every_declared_symbol_is_exported(wb):
+    lib = wb.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_argument_errors_without_gpu(wb):
+    with pytest.raises(wb.WbprError) as e:
+        wb.wbpr_build(3, 1, [0], [1], [1], 0, 0)          # s == t
+    assert e.value.status == -1
+    with pytest.raises(wb.WbprError) as e:
+        wb.wbpr_build(1, 0, [], [], [], 0, 0)             # n < 2
+    assert e.value.status == -1
+    with pytest.raises(wb.WbprError) as e:
+        wb.wbpr_build(1 << 30, 0, [], [], [], 0, 1)       # n too large
+    assert e.value.status == -5
+    with pytest.raises(wb.WbprError) as e:
+        wb.wbpr_build(4, 1, [0], [1], [1], 0, 1, layout=7)
+    assert e.value.status == -1
+    o = wb.wbpr_default_options()
+    assert o.use_rev == 1 and o.gap == 1 and o.small_tile == 8
+    o.small_tile = 5
+    with pytest.raises(wb.WbprError):
+        wb.wbpr_build(4, 1, [0], [1], [1], 0, 1, opts=o)
+    assert wb.wbpr_error_string(-4).startswith("iteration cap")
+
+
+def test_layout_restatement_by_hand(oracle_mod):
+    from oracle import layouts
+    # diamond: 0->1 (3), 0->2 (2), 1->2 (1), 1->3 (2), 2->3 (3)
+    src, dst, cap = [0, 0, 1, 1, 2], [1, 2, 2, 3, 3], [3, 2, 1, 2, 3]
+    b = layouts.bcsr(4, src, dst, cap)
+    # rows: 0:[1,2]  1:[0,2,3]  2:[0,1,3]  3:[1,2]
+    assert list(b["offsets"]) == [0, 2, 5, 8, 10]
+    assert list(b["col"]) == [1, 2, 0, 2, 3, 0, 1, 3, 1, 2]
+    assert list(b["cap"]) == [3, 2, 0, 1, 2, 0, 0, 3, 0, 0]
+    assert list(b["rev"]) == [2, 5, 0, 6, 8, 1, 3, 9, 4, 7]
+    assert list(b["arc2slot"]) == [0, 1, 3, 4, 7]
+    # merged antiparallel pair and duplicates: 0->1 (4), 1->0 (7), 0->1 (2), loop 1->1
+    b = layouts.bcsr(2, [0, 1, 0, 1], [1, 0, 1, 1], [4, 7, 2, 9])
+    assert list(b["col"]) == [1, 0] and list(b["cap"]) == [6, 7]
+    assert list(b["arc2slot"]) == [0, 1, 0, 0xFFFFFFFF]
+    r = layouts.rcsr(4, src, dst, cap)
+    assert list(r["offsets"]) == [0, 2, 4, 5, 5]
+    assert list(r["col"]) == [1, 2, 2, 3, 3]
+    assert list(r["in_offsets"]) == [0, 0, 1, 3, 5]
+    assert list(r["in_col"]) == [0, 0, 1, 1, 2]
+    assert list(r["flow_idx"]) == [0, 1, 2, 3, 4]
