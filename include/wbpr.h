@@ -62,18 +62,27 @@ typedef struct wbpr_options {
     int32_t use_rev;          /* BCSR backward-slot lookup: 1 = reverse index (default),
                                  0 = binary search in the neighbour's row (§3.2) */
     int32_t gap;              /* 1 = gap heuristic on (default), 0 = off */
+    int32_t multi_push;       /* 1 = discharge pass: the owner of u pushes along every
+                                 arc read as lower in one pass, then relabels if excess
+                                 is left (default); 0 = one push to the lowest
+                                 neighbour or one relabel per iteration (Alg. 1, 2) */
     int32_t cycle;            /* push-relabel iterations between global relabels
                                  (the "cycle" of Alg. 1); 0 = automatic */
     int32_t small_max_degree; /* rows up to this length get a tile of
                                  `small_tile` lanes (default 8) */
     int32_t small_tile;       /* 4, 8 or 16 lanes (default 8) */
     int32_t warp_max_degree;  /* longer rows (up to this) get one warp; longer
-                                 still get a whole thread block (default 2048) */
+                                 rows (hubs) are split into chunks of 2048 entries
+                                 that whole thread blocks take (default 256) */
     int32_t grid_blocks;      /* persistent grid size; 0 = automatic.  Clamped to
                                  the number of co-resident blocks. */
     int32_t barrier_timeout_ms; /* device wait limit (default 20000) */
     int64_t max_iterations;   /* cap on push-relabel iterations per solve
                                  (default 2^40); reaching it gives WBPR_ETIMEOUT */
+    int32_t trace;            /* > 0: record up to this many grid barriers of each
+                                 solve (barrier id, queue generation, device time in ns,
+                                 queue sizes); read with wbpr_export(WBPR_ARRAY_TRACE) */
+    int32_t reserved;
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */
@@ -235,7 +244,11 @@ enum {
     WBPR_ARRAY_IN_COL = 10,     /* int32[slots]: RCSR in-arc tail */
     WBPR_ARRAY_FLOW_IDX = 11,   /* uint32[slots]: RCSR in-arc -> out slot */
     WBPR_ARRAY_ARC2SLOT = 12,   /* uint32[m]: input arc -> slot (UINT32_MAX for loops) */
-    WBPR_ARRAY_EXCESS_TOTAL = 13 /* int64[1] */
+    WBPR_ARRAY_EXCESS_TOTAL = 13, /* int64[1] */
+    WBPR_ARRAY_TRACE = 14,       /* uint64[4 * records]: per grid barrier of the last
+                                    launch: barrier id, queue generation, globaltimer ns,
+                                    queue sizes (24 bits per tile class) */
+    WBPR_ARRAY_TRACE_LEN = 15    /* uint32[1]: records in the trace */
 };
 wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg);
 wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64_t count);

@@ -34,7 +34,8 @@ STAGE_PREFLOW, STAGE_GLOBAL_RELABEL, STAGE_ITERATIONS = 1, 2, 3
 ARRAY = {"height": (1, np.int32), "excess": (2, np.int64), "offsets": (3, np.int64),
          "col": (4, np.int32), "cf": (5, np.int32), "cap": (6, np.int32), "rev": (7, np.uint32),
          "bf": (8, np.int32), "in_offsets": (9, np.int64), "in_col": (10, np.int32),
-         "flow_idx": (11, np.uint32), "arc2slot": (12, np.uint32), "excess_total": (13, np.int64)}
+         "flow_idx": (11, np.uint32), "arc2slot": (12, np.uint32), "excess_total": (13, np.int64),
+         "trace": (14, np.uint64), "trace_len": (15, np.uint32)}
 
 # Every function declared in include/wbpr.h.
 EXPORTED_SYMBOLS = [
@@ -53,10 +54,12 @@ class WbprError(RuntimeError):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("use_rev", ctypes.c_int32), ("gap", ctypes.c_int32), ("cycle", ctypes.c_int32),
+    _fields_ = [("use_rev", ctypes.c_int32), ("gap", ctypes.c_int32),
+                ("multi_push", ctypes.c_int32), ("cycle", ctypes.c_int32),
                 ("small_max_degree", ctypes.c_int32), ("small_tile", ctypes.c_int32),
                 ("warp_max_degree", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
-                ("barrier_timeout_ms", ctypes.c_int32), ("max_iterations", ctypes.c_int64)]
+                ("barrier_timeout_ms", ctypes.c_int32), ("max_iterations", ctypes.c_int64),
+                ("trace", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -332,6 +335,11 @@ def wbpr_export(g: Graph, what: str, count: int | None = None) -> np.ndarray:
         count = {"height": info["n"], "excess": info["n"], "offsets": info["n"] + 1,
                  "in_offsets": info["n"] + 1, "arc2slot": info["m"], "excess_total": 1}.get(
                      what, info["slots"])
+    if what == "trace":
+        length = wbpr_export(g, "trace_len", 1)[0] if wbpr_get_options(g).trace > 0 else 0
+        out = np.zeros(4 * int(length), dtype=dt)
+        _check(load().wbpr_export(g.handle, code, out.ctypes.data if length else None, out.size))
+        return out.reshape(-1, 4)
     out = np.zeros(count, dtype=dt)
     _check(load().wbpr_export(g.handle, code, out.ctypes.data if count else None, int(count)))
     return out

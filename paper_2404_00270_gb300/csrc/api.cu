@@ -81,10 +81,11 @@ void wbpr_default_options(wbpr_options *o)
     memset(o, 0, sizeof(*o));
     o->use_rev = 1;
     o->gap = 1;
+    o->multi_push = 1;
     o->cycle = 0;
     o->small_max_degree = 8;
     o->small_tile = 8;
-    o->warp_max_degree = 2048;
+    o->warp_max_degree = 256;
     o->grid_blocks = 0;
     o->barrier_timeout_ms = 20000;
     o->max_iterations = (int64_t)1 << 40;
@@ -122,10 +123,12 @@ static wbpr_status check_options(const wbpr_options *o)
 {
     if (o->use_rev != 0 && o->use_rev != 1) return WBPR_EINVAL;
     if (o->gap != 0 && o->gap != 1) return WBPR_EINVAL;
+    if (o->multi_push != 0 && o->multi_push != 1) return WBPR_EINVAL;
     if (o->cycle < 0) return WBPR_EINVAL;
     if (o->small_tile != 4 && o->small_tile != 8 && o->small_tile != 16) return WBPR_EINVAL;
     if (o->small_max_degree < 0 || o->warp_max_degree < o->small_max_degree) return WBPR_EINVAL;
     if (o->grid_blocks < 0 || o->barrier_timeout_ms <= 0 || o->max_iterations <= 0) return WBPR_EINVAL;
+    if (o->trace < 0 || o->trace > (1 << 24)) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -158,8 +161,14 @@ static wbpr_status alloc_state(wbpr_graph *g, cudaStream_t st)
     STATE_ALLOC(g->h, int, n);
     STATE_ALLOC(g->dead, unsigned char, n);
     STATE_ALLOC(g->count, int, n + 1);
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
         for (int k = 0; k < kClasses; ++k) STATE_ALLOC(g->q[a][k], int, n);
+        STATE_ALLOC(g->hub_start[a], unsigned, n);
+        STATE_ALLOC(g->hub_e0[a], long long, n);
+        STATE_ALLOC(g->hub_rem[a], long long, n);
+        STATE_ALLOC(g->hub_aux[a], unsigned long long, n);
+        STATE_ALLOC(g->hub_done[a], unsigned, n);
+    }
     STATE_ALLOC(g->ctl, Ctl, 1);
     int per_sm = 0;
     API_CUDA(solver_max_blocks_per_sm(g->layout, 8, &per_sm));
@@ -369,18 +378,33 @@ static Params make_params(wbpr_graph *g, int mode)
     p.st.h = g->h;
     p.st.dead = g->dead;
     p.st.count = g->count;
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
         for (int k = 0; k < kClasses; ++k) p.st.q[a][k] = g->q[a][k];
+        p.st.hub_start[a] = g->hub_start[a];
+        p.st.hub_e0[a] = g->hub_e0[a];
+        p.st.hub_rem[a] = g->hub_rem[a];
+        p.st.hub_aux[a] = g->hub_aux[a];
+        p.st.hub_done[a] = g->hub_done[a];
+    }
     p.st.ctl = g->ctl;
     p.st.bstats = g->bstats;
     p.mode = mode;
     p.cycle = g->opts.cycle > 0 ? g->opts.cycle : auto_cycle(g);
     p.gap = g->opts.gap;
+    p.multi_push = g->opts.multi_push;
     p.use_rev = g->layout == WBPR_BCSR ? g->opts.use_rev : 0;
     p.small_max = g->opts.small_max_degree;
     p.warp_max = g->opts.warp_max_degree;
     p.max_iterations = g->opts.max_iterations;
     p.timeout_ns = (unsigned long long)g->opts.barrier_timeout_ms * 1000000ull;
+    if (g->opts.trace > 0) {
+        if (!g->trace || g->trace_cap < g->opts.trace) {
+            g->trace = (unsigned long long *)g->alloc(sizeof(unsigned long long) * 4 * (size_t)g->opts.trace, 0);
+            g->trace_cap = g->trace ? g->opts.trace : 0;
+        }
+        p.trace = g->trace;
+        p.trace_cap = g->trace_cap;
+    }
     return p;
 }
 
@@ -624,6 +648,15 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
     case WBPR_ARRAY_FLOW_IDX: src = g->flow_idx; avail = g->flow_idx ? g->slots : 0; break;
     case WBPR_ARRAY_ARC2SLOT: src = g->arc2slot; avail = g->m; break;
     case WBPR_ARRAY_EXCESS_TOTAL: src = &g->ctl->excess_total; elem = 8; avail = 1; break;
+    case WBPR_ARRAY_TRACE_LEN: src = &g->ctl->trace_len; elem = 4; avail = 1; break;
+    case WBPR_ARRAY_TRACE: {
+        unsigned len = 0;
+        if (g->trace) API_CUDA(cudaMemcpy(&len, &g->ctl->trace_len, sizeof(len), cudaMemcpyDeviceToHost));
+        src = g->trace;
+        elem = 8;
+        avail = 4 * (int64_t)len;
+        break;
+    }
     default: return set_error(WBPR_EINVAL, "wbpr_export: unknown array");
     }
     if (count > avail) return set_error(WBPR_EINVAL, "wbpr_export: count exceeds the array");

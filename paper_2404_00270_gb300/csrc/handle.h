@@ -55,8 +55,15 @@ struct wbpr_graph {
     unsigned char *dead = nullptr;
     int *count = nullptr;
     int *q[2][wbpr::kClasses] = {{nullptr}};
+    unsigned *hub_start[2] = {nullptr, nullptr};
+    long long *hub_e0[2] = {nullptr, nullptr};
+    long long *hub_rem[2] = {nullptr, nullptr};
+    unsigned long long *hub_aux[2] = {nullptr, nullptr};
+    unsigned *hub_done[2] = {nullptr, nullptr};
     wbpr::Ctl *ctl = nullptr;
     long long *bstats = nullptr;
+    unsigned long long *trace = nullptr;  // optional barrier trace (wbpr_options.trace)
+    int trace_cap = 0;
     int bstats_blocks = 0;
     int *edge_tmp = nullptr;           // device staging of edge flows for host outputs
     unsigned char *side_tmp = nullptr; // device staging of the cut side for host outputs

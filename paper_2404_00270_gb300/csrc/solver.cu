@@ -84,8 +84,12 @@ struct Smem {
     unsigned qbase[kClasses];
     u64 red[kWarps];
     long long red64[kWarps];
+    long long wsum[kWarps];
+    long long bcast64;
+    int bcast32;
     long long stats[kStatCount];
     unsigned item;
+    unsigned hub_pos, hub_j, hub_nch;
     int ok;
 };
 
@@ -104,11 +108,11 @@ __device__ bool grid_sync(Ctx &c, int where)
         Ctl *ctl = c.P.st.ctl;
         c.bar_target += gridDim.x;
         __threadfence();
-        atomicAdd(&ctl->bar, 1ULL);
+        if (gridDim.x > 1) atomicAdd(&ctl->bar, 1ULL);
         int ok = 1;
         u64 t0 = 0;
         unsigned spins = 0;
-        while (ld_acquire(&ctl->bar) < c.bar_target) {
+        while (gridDim.x > 1 && ld_acquire(&ctl->bar) < c.bar_target) {
             if (ld_err(ctl) != 0) { ok = 0; break; }
             ++spins;
             if ((spins & 255u) == 0) {
@@ -122,11 +126,24 @@ __device__ bool grid_sync(Ctx &c, int where)
                     break;
                 }
             }
-            if (spins > 32) __nanosleep(40);
+            if (spins > 64) __nanosleep(20);
         }
         __threadfence();
         if (ld_err(ctl) != 0) ok = 0;
         c.sm.ok = ok;
+        if (c.P.trace && blockIdx.x == 0) {
+            unsigned i = ctl->trace_len;
+            if (i < (unsigned)c.P.trace_cap) {
+                const unsigned *q = ctl->q_count[c.gen % 3];
+                const u64 hubs = ctl->hub_pack[c.gen % 3] >> 40;
+                u64 *r = c.P.trace + 4ull * i;
+                r[0] = (u64)where;
+                r[1] = (u64)c.gen;
+                r[2] = global_ns();
+                r[3] = (u64)q[0] | ((u64)q[1] << 24) | (hubs << 48);
+                ctl->trace_len = i + 1;
+            }
+        }
     }
     __syncthreads();
     return c.sm.ok != 0;
@@ -188,8 +205,89 @@ __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
         int z = (gen + 2) % 3;
         for (int k = 0; k < kClasses; ++k) ctl->q_count[z][k] = 0;
         ctl->q_grab[z] = 0;
+        ctl->hub_pack[z] = 0;
         ctl->gap_level[z] = kUnvisited;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Hub class: a vertex whose residual list is longer than warp_max is split
+// into chunks of kChunk entries.  One 64-bit atomic gives it both its queue
+// position and the id of its first chunk, so chunk ids grow with the
+// position and a chunk id maps back to its hub by binary search.
+// ---------------------------------------------------------------------------
+constexpr u64 kChunkMask = (1ull << 40) - 1;
+
+__device__ __forceinline__ unsigned hub_chunks(long long deg)
+{
+    return deg <= 0 ? 1u : (unsigned)((deg + kChunk - 1) / kChunk);
+}
+
+__device__ __forceinline__ void hub_append(Ctx &c, int slot3, int set, int v, long long deg, bool pr,
+                                           long long ev)
+{
+    const StateDev &st = c.P.st;
+    const u64 old = atomicAdd(&st.ctl->hub_pack[slot3], (1ull << 40) | hub_chunks(deg));
+    const unsigned pos = (unsigned)(old >> 40);
+    st.q[set][2][pos] = v;
+    st.hub_start[set][pos] = (unsigned)(old & kChunkMask);
+    if (pr) {
+        st.hub_e0[set][pos] = ev;
+        st.hub_rem[set][pos] = ev;
+        st.hub_aux[set][pos] = kNoKey;
+        st.hub_done[set][pos] = 0;
+    }
+}
+
+__device__ __forceinline__ unsigned queue_total(const Ctl *ctl, int gen)
+{
+    const int s3 = gen % 3;
+    return __ldcg(&ctl->q_count[s3][0]) + __ldcg(&ctl->q_count[s3][1]) +
+           (unsigned)(__ldcg(&ctl->hub_pack[s3]) >> 40);
+}
+
+// Take the next hub chunk of generation (s3, set).  Block-uniform result.
+__device__ bool grab_chunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks, unsigned &pos,
+                           unsigned &j, unsigned &nch)
+{
+    if (threadIdx.x == 0) {
+        const unsigned id = atomicAdd(&c.P.st.ctl->q_grab[s3], 1u);
+        if (id < nchunks) {
+            const unsigned *start = c.P.st.hub_start[set];
+            unsigned lo = 0, hi = nh;  // start[lo] <= id < start[hi]
+            while (hi - lo > 1) {
+                unsigned mid = (lo + hi) >> 1;
+                if (__ldcg(start + mid) <= id) lo = mid;
+                else hi = mid;
+            }
+            const unsigned s0 = __ldcg(start + lo);
+            const unsigned s1 = lo + 1 < nh ? __ldcg(start + lo + 1) : nchunks;
+            c.sm.hub_pos = lo;
+            c.sm.hub_j = id - s0;
+            c.sm.hub_nch = s1 - s0;
+        }
+        c.sm.item = id;
+    }
+    __syncthreads();
+    const bool ok = c.sm.item < nchunks;
+    pos = c.sm.hub_pos;
+    j = c.sm.hub_j;
+    nch = c.sm.hub_nch;
+    __syncthreads();
+    return ok;
+}
+
+// Row index r of u's residual list -> slot (RCSR: out entries, then in entries).
+template <int L>
+__device__ __forceinline__ long long row_slot(long long ob, long long dout, long long ib, long long r,
+                                              bool &in)
+{
+    if (L == kBCSR || r < dout) {
+        in = false;
+        return ob + r;
+    }
+    in = true;
+    return ib + (r - dout);
 }
 
 __device__ long long block_sum(Ctx &c, long long x)
@@ -283,6 +381,22 @@ __device__ __forceinline__ long long lower_bound_col(const int *col, long long b
     return b;
 }
 
+// Relabel u from hu to hn (capped at hcap) and keep the gap counts.
+__device__ __forceinline__ void relabel_to(Ctx &c, int u, int hu, int hn, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    if (hn > hcap) hn = hcap;
+    __stcg(P.st.h + u, hn);
+    atomicAdd((unsigned long long *)&c.sm.stats[kStatRelabels], 1ull);
+    if (phase1 && P.gap) {
+        int *count = P.st.count;
+        const int n = P.g.n;
+        if (hn < n) atomicAdd(count + hn, 1);
+        int prev = atomicSub(count + hu, 1);
+        if (prev == 1) atomicMin(&P.st.ctl->gap_level[c.gen % 3], hu);
+    }
+}
+
 // Push or relabel for the owner of u (one thread).  Alg. 1: if h(u) > h'
 // push d = min(e(u), cf(u, v')) with four atomics, else h(u) = h' + 1.
 template <int L>
@@ -341,16 +455,7 @@ __device__ void apply_op(Ctx &c, int u, u64 key, bool phase1, int hcap)
         }
     }
     int hn = (key == kNoKey) ? hcap : (int)(key >> 32) + 1;
-    if (hn > hcap) hn = hcap;
-    __stcg(h + u, hn);
-    atomicAdd((unsigned long long *)&c.sm.stats[kStatRelabels], 1ull);
-    if (phase1 && P.gap) {
-        int *count = P.st.count;
-        const int n = g.n;
-        if (hn < n) atomicAdd(count + hn, 1);
-        int prev = atomicSub(count + hu, 1);
-        if (prev == 1) atomicMin(&P.st.ctl->gap_level[c.gen % 3], hu);
-    }
+    relabel_to(c, u, hu, hn, phase1, hcap);
 }
 
 // Tile of W <= 32 lanes (all 32 lanes of the warp call this; u < 0 = idle).
@@ -381,24 +486,291 @@ __device__ void pr_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
     }
 }
 
-template <int L>
-__device__ void pr_block(Ctx &c, int u, bool phase1, int hcap)
+// ---------------------------------------------------------------------------
+// Discharge pass (multi-push).  The owner tile of u reads e(u) = E and h(u)
+// once, then walks u's residual list: every arc read as lower (cf > 0 and
+// h(v) < h(u)) is admissible, and the tile splits the remaining excess over
+// the admissible arcs of each chunk in slot order with an inclusive prefix
+// sum of their capacities, so every lane pushes min(cf, what is left before
+// it).  Each push is the push of Alg. 1 (relaxed condition h(u) > h(v) on
+// the heights read); several of them per pass replace one push per
+// iteration.  If excess is left after the whole list, every arc still
+// residual was read at a height >= h(u) and u is relabelled to one above the
+// lowest of them.  The pass stops reading as soon as the excess is gone.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ long long seg_incl_scan(long long x, int sl)
 {
-    const GraphDev &g = c.P.g;
-    long long ob = __ldg(g.off + u), oe = __ldg(g.off + u + 1), ib = 0, ie = 0;
-    int ro = (int)((oe - ob + kBlock - 1) / kBlock), ri = 0;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        long long y = __shfl_up_sync(kFull, x, o, W);
+        if (sl >= o) x += y;
+    }
+    return x;
+}
+
+template <int W>
+__device__ __forceinline__ int seg_min_int(int x)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+        int y = __shfl_xor_sync(kFull, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+template <int W>
+__device__ __forceinline__ int seg_sum_int(int x)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// Load entry k of u's list: residual capacity and neighbour (and its height
+// when residual).  `in` selects the RCSR in-list.
+template <int L>
+__device__ __forceinline__ void mp_load(const Params &P, long long k, bool in, int &cap, int &v,
+                                        int &hv)
+{
+    const GraphDev &g = P.g;
+    if (L == kRCSR && in) {
+        unsigned j = __ldg(g.flow_idx + k);
+        cap = __ldcg(g.bf + j);
+        v = __ldg(g.in_col + k);
+    } else {
+        cap = __ldcg(g.cf + k);
+        v = __ldg(g.col + k);
+    }
+    hv = cap > 0 ? __ldcg(P.st.h + v) : 0x7fffffff;
+}
+
+// Push d along entry k of u's list.
+template <int L>
+__device__ __forceinline__ void mp_push(const Params &P, int u, long long k, bool in, int v, int d)
+{
+    const GraphDev &g = P.g;
+    int *dec;
+    int *inc;
+    if (L == kBCSR) {
+        long long ra = P.use_rev ? (long long)__ldg(g.rev + k)
+                                 : lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), u);
+        dec = g.cf + k;
+        inc = g.cf + ra;
+    } else if (!in) {
+        dec = g.cf + k;
+        inc = g.bf + k;
+    } else {
+        unsigned j = __ldg(g.flow_idx + k);
+        dec = g.bf + j;
+        inc = g.cf + j;
+    }
+    atomicSub(dec, d);
+    atomicAdd(inc, d);
+    atomicAdd((u64 *)(P.st.e + v), (u64)(long long)d);
+}
+
+template <int L, int W>
+__device__ __forceinline__ void mp_list(Ctx &c, int u, long long b, long long e, int rounds, bool in,
+                                        int sl, int hu, long long &rem, int &hres, int &npush,
+                                        long long &scanned)
+{
+    const Params &P = c.P;
+    for (int r = 0; r < rounds; ++r) {
+        if (__all_sync(kFull, rem == 0)) break;
+        const long long base = b + (long long)r * W;
+        const long long k = base + sl;
+        int cap = 0, v = 0, hv = 0x7fffffff;
+        if (rem > 0 && k < e) mp_load<L>(P, k, in, cap, v, hv);
+        if (rem > 0 && base < e) scanned += (e - base < W) ? (e - base) : W;
+        long long amt = (cap > 0 && hv < hu && rem > 0) ? (long long)cap : 0;
+        long long incl = seg_incl_scan<W>(amt, sl);
+        long long tot = __shfl_sync(kFull, incl, W - 1, W);
+        long long d = rem - (incl - amt);
+        d = d < 0 ? 0 : (d > amt ? amt : d);
+        if (d > 0) {
+            mp_push<L>(P, u, k, in, v, (int)d);
+            ++npush;
+        }
+        if ((long long)cap - d > 0 && hv < hres) hres = hv;
+        rem -= tot < rem ? tot : rem;
+    }
+}
+
+template <int L, int W>
+__device__ void mp_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    long long ob = 0, oe = 0, ib = 0, ie = 0;
+    int ro = 0, ri = 0;
+    long long E = 0;
+    int hu = 0;
+    if (u >= 0) {
+        ob = __ldg(g.off + u);
+        oe = __ldg(g.off + u + 1);
+        ro = (int)((oe - ob + W - 1) / W);
+        if (L == kRCSR) {
+            ib = __ldg(g.in_off + u);
+            ie = __ldg(g.in_off + u + 1);
+            ri = (int)((ie - ib + W - 1) / W);
+        }
+        if (sl == 0) {
+            E = __ldcg(P.st.e + u);
+            hu = __ldcg(P.st.h + u);
+        }
+    }
+    E = __shfl_sync(kFull, E, 0, W);
+    hu = __shfl_sync(kFull, hu, 0, W);
+    ro = __reduce_max_sync(kFull, ro);
+    if (L == kRCSR) ri = __reduce_max_sync(kFull, ri);
+    long long rem = E;
+    int hres = 0x7fffffff, npush = 0;
+    long long scanned = 0;
+    mp_list<L, W>(c, u, ob, oe, ro, false, sl, hu, rem, hres, npush, scanned);
+    if (L == kRCSR) mp_list<L, W>(c, u, ib, ie, ri, true, sl, hu, rem, hres, npush, scanned);
+    hres = seg_min_int<W>(hres);
+    npush = seg_sum_int<W>(npush);
+    if (u >= 0 && sl == 0) {
+        const long long D = E - rem;
+        if (D > 0) atomicAdd((u64 *)(P.st.e + u), (u64)(-D));
+        if (npush) atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], (u64)npush);
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)scanned);
+        if (rem > 0) relabel_to(c, u, hu, hres == 0x7fffffff ? hcap : hres + 1, phase1, hcap);
+    }
+}
+
+// Block-wide inclusive scan of x; *tot receives the block total.
+__device__ __forceinline__ long long block_incl_scan(Ctx &c, long long x, long long *tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    x = seg_incl_scan<32>(x, lane);
+    if (lane == 31) c.sm.wsum[warp] = x;
+    __syncthreads();
+    long long before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        long long y = c.sm.wsum[w];
+        if (w < warp) before += y;
+        all += y;
+    }
+    __syncthreads();
+    *tot = all;
+    return x + before;
+}
+
+// One chunk of a hub's residual list, processed by one block.  Multi-push:
+// the chunk sums the capacity of its admissible entries, takes up to that
+// much of the hub's remaining excess with a compare-and-swap on the hub's
+// budget, and spreads what it took over its admissible entries with a block
+// prefix sum.  Single push: the chunk's minimum (height, row index) key.
+// The last chunk of the hub to finish lowers e(u) by what all chunks pushed
+// and relabels u when excess is left (or applies the single push/relabel).
+template <int L>
+__device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch, bool phase1,
+                         int hcap)
+{
+    constexpr int kPer = kChunk / kBlock;
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int u = __ldcg(P.st.q[set][2] + pos);
+    const long long ob = __ldg(g.off + u), dout = __ldg(g.off + u + 1) - ob;
+    long long ib = 0, din = 0;
     if (L == kRCSR) {
         ib = __ldg(g.in_off + u);
-        ie = __ldg(g.in_off + u + 1);
-        ri = (int)((ie - ib + kBlock - 1) / kBlock);
+        din = __ldg(g.in_off + u + 1) - ib;
     }
-    u64 best = (L == kBCSR)
-                   ? scan_bcsr<kBlock>(g, c.P.st.h, ob, oe, threadIdx.x, ro)
-                   : scan_rcsr<kBlock>(g, c.P.st.h, ob, oe, ib, ie, threadIdx.x, ro, ri);
-    best = block_min(c, best);
+    const long long deg = dout + din;
+    const long long r0 = (long long)j * kChunk;
+    const long long r1 = deg < r0 + kChunk ? deg : r0 + kChunk;
+    const int hu = __ldcg(P.st.h + u);
+    int capv[kPer], vv[kPer], hvv[kPer];
+    long long asum = 0;
+    u64 best = kNoKey;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const long long r = r0 + threadIdx.x + (long long)i * kBlock;
+        capv[i] = 0;
+        vv[i] = 0;
+        hvv[i] = 0x7fffffff;
+        if (r < r1) {
+            bool in;
+            const long long k = row_slot<L>(ob, dout, ib, r, in);
+            mp_load<L>(P, k, in, capv[i], vv[i], hvv[i]);
+            if (capv[i] > 0) {
+                if (hvv[i] < hu) asum += capv[i];
+                best = umin64(best, make_key(hvv[i], (unsigned)r));
+            }
+        }
+    }
+    if (threadIdx.x == 0 && r1 > r0)
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)(r1 - r0));
+    if (!P.multi_push) {
+        best = block_min(c, best);
+        if (threadIdx.x == 0 && best != kNoKey) atomicMin(P.st.hub_aux[set] + pos, best);
+    } else {
+        long long tot;
+        const long long incl = block_incl_scan(c, asum, &tot);
+        if (threadIdx.x == 0) {
+            long long take = 0;
+            if (tot > 0) {
+                long long *rp = P.st.hub_rem[set] + pos;
+                long long r = __ldcg(rp);
+                for (int tries = 0; tries < (1 << 20) && r > 0; ++tries) {
+                    const long long t = r < tot ? r : tot;
+                    const long long prev = (long long)atomicCAS((u64 *)rp, (u64)r, (u64)(r - t));
+                    if (prev == r) {
+                        take = t;
+                        break;
+                    }
+                    r = prev;
+                }
+            }
+            c.sm.bcast64 = take;
+        }
+        __syncthreads();
+        long long budget = c.sm.bcast64 - (incl - asum);
+        budget = budget < 0 ? 0 : (budget > asum ? asum : budget);
+        int npush = 0, hres = 0x7fffffff;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            int cap = capv[i];
+            if (cap > 0 && hvv[i] < hu && budget > 0) {
+                const long long r = r0 + threadIdx.x + (long long)i * kBlock;
+                bool in;
+                const long long k = row_slot<L>(ob, dout, ib, r, in);
+                const int d = (int)(budget < cap ? budget : cap);
+                mp_push<L>(P, u, k, in, vv[i], d);
+                budget -= d;
+                cap -= d;
+                ++npush;
+            }
+            if (cap > 0 && hvv[i] < hres) hres = hvv[i];
+        }
+        const u64 key = block_min(c, (u64)(unsigned)hres << 32);
+        const long long np = block_sum(c, npush);
+        if (threadIdx.x == 0) {
+            if ((int)(key >> 32) != 0x7fffffff) atomicMin(P.st.hub_aux[set] + pos, key);
+            if (np) atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], (u64)np);
+        }
+    }
+    __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) {
-        atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)((oe - ob) + (ie - ib)));
-        apply_op<L>(c, u, best, phase1, hcap);
+        const unsigned done = atomicAdd(P.st.hub_done[set] + pos, 1u);
+        if (done + 1 == nch) {
+            __threadfence();
+            const u64 key = __ldcg(P.st.hub_aux[set] + pos);
+            if (!P.multi_push) {
+                apply_op<L>(c, u, key, phase1, hcap);
+            } else {
+                const long long rem = __ldcg(P.st.hub_rem[set] + pos);
+                const long long D = __ldcg(P.st.hub_e0[set] + pos) - rem;
+                if (D > 0) atomicAdd((u64 *)(P.st.e + u), (u64)(-D));
+                if (rem > 0) relabel_to(c, u, hu, key == kNoKey ? hcap : (int)(key >> 32) + 1, phase1, hcap);
+            }
+        }
     }
     __syncthreads();
 }
@@ -413,25 +785,23 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
     reset_rotating(c, gen);
     const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
-    const unsigned c2 = __ldcg(&ctl->q_count[s3][2]);
-    // hub rows: one block each, taken dynamically
-    if (c2) {
-        const int *q2 = P.st.q[set][2];
-        for (;;) {
-            if (threadIdx.x == 0) c.sm.item = atomicAdd(&ctl->q_grab[s3], 1u);
-            __syncthreads();
-            unsigned i = c.sm.item;
-            __syncthreads();
-            if (i >= c2) break;
-            pr_block<L>(c, __ldcg(q2 + i), phase1, hcap);
-        }
+    // hub rows: chunks taken dynamically, one block each
+    {
+        const u64 hp = __ldcg(&ctl->hub_pack[s3]);
+        const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
+        unsigned pos, j, nch;
+        if (nchunks)
+            while (grab_chunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_chunk<L>(c, set, pos, j, nch, phase1, hcap);
     }
     const int lane = threadIdx.x & 31;
     const unsigned gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const unsigned nwarps = gridDim.x * kWarps;
     {
         const int *q1 = P.st.q[set][1];
-        for (unsigned i = gwarp; i < c1; i += nwarps) pr_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
+        for (unsigned i = gwarp; i < c1; i += nwarps) {
+            if (P.multi_push) mp_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
+            else pr_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
+        }
     }
     {
         constexpr unsigned TPW = 32 / SW;
@@ -443,7 +813,8 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
             for (unsigned r = 0; r < rounds; ++r) {
                 unsigned i = gt0 + sub + r * ntiles;
                 int u = i < c0 ? __ldcg(q0 + i) : -1;
-                pr_tile<L, SW>(c, u, sl, phase1, hcap);
+                if (P.multi_push) mp_tile<L, SW>(c, u, sl, phase1, hcap);
+                else pr_tile<L, SW>(c, u, sl, phase1, hcap);
             }
         }
     }
@@ -477,8 +848,12 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
                 ++lifted;
             }
             if (v != s && v != t && hv < hcap) {
-                if (__ldcg(P.st.e + v) > 0) {
-                    q_append(c, s3, set, classify(P, degree<L>(g, (int)v)), (int)v);
+                const long long ev = __ldcg(P.st.e + v);
+                if (ev > 0) {
+                    const long long d = degree<L>(g, (int)v);
+                    const int cls = classify(P, d);
+                    if (cls == 2) hub_append(c, s3, set, (int)v, d, true, ev);
+                    else q_append(c, s3, set, cls, (int)v);
                     ++nact;
                 }
             }
@@ -486,7 +861,6 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
         __syncthreads();
         unsigned mx = c.sm.qcnt[0];
         if (c.sm.qcnt[1] > mx) mx = c.sm.qcnt[1];
-        if (c.sm.qcnt[2] > mx) mx = c.sm.qcnt[2];
         __syncthreads();  // every thread has read the counts before new appends
         if (mx > (unsigned)(kQueueCap - kBlock)) q_flush(c, s3, set);
     }
@@ -534,14 +908,19 @@ template <int L, int DIR>
 __device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int n3)
 {
     const Params &P = c.P;
+    bool fresh;
     if (DIR == kBfsBackward) {
         int *h = P.st.h;
-        if (__ldcg(h + v) == kUnvisited && atomicCAS(h + v, kUnvisited, val) == kUnvisited)
-            q_append(c, n3, nset, classify(P, degree<L>(P.g, v)), v);
+        fresh = __ldcg(h + v) == kUnvisited && atomicCAS(h + v, kUnvisited, val) == kUnvisited;
     } else {
         int *mark = P.st.count;
-        if (__ldcg(mark + v) == 0 && atomicCAS(mark + v, 0, 1) == 0)
-            q_append(c, n3, nset, classify(P, degree<L>(P.g, v)), v);
+        fresh = __ldcg(mark + v) == 0 && atomicCAS(mark + v, 0, 1) == 0;
+    }
+    if (fresh) {
+        const long long d = degree<L>(P.g, v);
+        const int cls = classify(P, d);
+        if (cls == 2) hub_append(c, n3, nset, v, d, false, 0);
+        else q_append(c, n3, nset, cls, v);
     }
 }
 
@@ -562,6 +941,30 @@ __device__ void bfs_row(Ctx &c, int w, int sl, int val, int nset, int n3)
     }
 }
 
+// Scan one chunk of frontier hub w with the whole block.
+template <int L, int DIR>
+__device__ long long bfs_chunk(Ctx &c, int set, unsigned pos, unsigned j, int val, int nset, int n3)
+{
+    const GraphDev &g = c.P.g;
+    const int w = __ldcg(c.P.st.q[set][2] + pos);
+    const long long ob = __ldg(g.off + w), dout = __ldg(g.off + w + 1) - ob;
+    long long ib = 0, din = 0;
+    if (L == kRCSR) {
+        ib = __ldg(g.in_off + w);
+        din = __ldg(g.in_off + w + 1) - ib;
+    }
+    const long long deg = dout + din;
+    const long long r0 = (long long)j * kChunk;
+    const long long r1 = deg < r0 + kChunk ? deg : r0 + kChunk;
+    for (long long r = r0 + threadIdx.x; r < r1; r += kBlock) {
+        bool in;
+        const long long k = row_slot<L>(ob, dout, ib, r, in);
+        if (residual_to<L, DIR>(c.P, k, in, w))
+            bfs_visit<L, DIR>(c, in ? __ldg(g.in_col + k) : __ldg(g.col + k), val, nset, n3);
+    }
+    return r1 > r0 ? r1 - r0 : 0;
+}
+
 // Consume frontier generation `gen`, produce generation gen + 1.
 template <int L, int DIR, int SW>
 __device__ void bfs_level(Ctx &c, int val)
@@ -573,24 +976,19 @@ __device__ void bfs_level(Ctx &c, int val)
     reset_rotating(c, gen);
     const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
-    const unsigned c2 = __ldcg(&ctl->q_count[s3][2]);
     long long scanned = 0;
-    if (c2) {
-        const int *q2 = P.st.q[set][2];
-        for (;;) {
-            if (threadIdx.x == 0) c.sm.item = atomicAdd(&ctl->q_grab[s3], 1u);
-            __syncthreads();
-            unsigned i = c.sm.item;
-            __syncthreads();
-            if (i >= c2) break;
-            int w = __ldcg(q2 + i);
-            bfs_row<L, DIR, kBlock>(c, w, threadIdx.x, val, nset, n3);
-            if (threadIdx.x == 0) scanned += degree<L>(P.g, w);
-            __syncthreads();
-            unsigned mx = c.sm.qcnt[0];
-            if (c.sm.qcnt[1] > mx) mx = c.sm.qcnt[1];
-            if (c.sm.qcnt[2] > mx) mx = c.sm.qcnt[2];
-            if (mx > (unsigned)(kQueueCap / 2)) q_flush(c, n3, nset);
+    {
+        const u64 hp = __ldcg(&ctl->hub_pack[s3]);
+        const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
+        unsigned pos, j, nch;
+        if (nchunks) {
+            while (grab_chunk(c, s3, set, nh, nchunks, pos, j, nch)) {
+                const long long k = bfs_chunk<L, DIR>(c, set, pos, j, val, nset, n3);
+                if (threadIdx.x == 0) scanned += k;
+                __syncthreads();
+                unsigned mx = c.sm.qcnt[0] > c.sm.qcnt[1] ? c.sm.qcnt[0] : c.sm.qcnt[1];
+                if (mx > (unsigned)(kQueueCap / 2)) q_flush(c, n3, nset);
+            }
         }
     }
     const int lane = threadIdx.x & 31;
@@ -619,11 +1017,20 @@ __device__ void bfs_level(Ctx &c, int val)
     if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
 }
 
-__device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v, int cls)
+// Seed a BFS: generation `gen` holds the single vertex v.
+template <int L>
+__device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long d = degree<L>(c.P.g, v);
+        const int cls = classify(c.P, d);
         c.P.st.q[gen & 1][cls][0] = v;
-        c.P.st.ctl->q_count[gen % 3][cls] = 1;
+        if (cls == 2) {
+            c.P.st.hub_start[gen & 1][0] = 0;
+            c.P.st.ctl->hub_pack[gen % 3] = (1ull << 40) | hub_chunks(d);
+        } else {
+            c.P.st.ctl->q_count[gen % 3][cls] = 1;
+        }
     }
 }
 
@@ -649,12 +1056,10 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
         if (phase1 && P.st.dead[v]) continue;
         __stcg(P.st.h + v, v == target ? base : kUnvisited);
     }
-    seed_queue(c, c.gen, target, classify(P, degree<L>(g, target)));
+    seed_queue<L>(c, c.gen, target);
     if (!grid_sync(c, 10)) return false;
     for (int level = 0;; ++level) {
-        const unsigned tot = __ldcg(&P.st.ctl->q_count[c.gen % 3][0]) +
-                             __ldcg(&P.st.ctl->q_count[c.gen % 3][1]) +
-                             __ldcg(&P.st.ctl->q_count[c.gen % 3][2]);
+        const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
         if (gap && blockIdx.x == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
         bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
@@ -691,9 +1096,7 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
     for (long long i = 0; i < max_it; ++i) {
         build_avq<L>(c, phase1, hcap);
         if (!grid_sync(c, 20)) return false;
-        const int s3 = c.gen % 3;
-        const unsigned tot = __ldcg(&P.st.ctl->q_count[s3][0]) + __ldcg(&P.st.ctl->q_count[s3][1]) +
-                             __ldcg(&P.st.ctl->q_count[s3][2]);
+        const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) {
             reset_rotating(c, c.gen);
             if (!grid_sync(c, 21)) return false;
@@ -798,12 +1201,10 @@ __device__ bool min_cut(Ctx &c)
     const long long tid = blockIdx.x * kBlock + threadIdx.x;
     int *mark = P.st.count;
     for (long long v = tid; v <= n; v += stride) __stcg(mark + v, v == g.s ? 1 : 0);
-    seed_queue(c, c.gen, g.s, classify(P, degree<L>(g, g.s)));
+    seed_queue<L>(c, c.gen, g.s);
     if (!grid_sync(c, 30)) return false;
     for (;;) {
-        const unsigned tot = __ldcg(&P.st.ctl->q_count[c.gen % 3][0]) +
-                             __ldcg(&P.st.ctl->q_count[c.gen % 3][1]) +
-                             __ldcg(&P.st.ctl->q_count[c.gen % 3][2]);
+        const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
         bfs_level<L, kBfsForward, SW>(c, 1);
         if (!grid_sync(c, 31)) return false;

@@ -26,6 +26,8 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kClasses = 3;         // tile classes: small tile, warp, block
 constexpr int kQueueCap = 1024;     // per-class shared-memory staging of queue appends
 constexpr int kUnvisited = 0x7fffffff;
+constexpr int kChunk = 2048;        // hub rows are processed in chunks of this many entries,
+                                    // one chunk per block, taken dynamically
 
 enum Layout : int { kRCSR = 0, kBCSR = 1 };
 
@@ -55,9 +57,11 @@ struct __align__(128) Ctl {
     long long phase1_iterations;
     long long global_relabels;
     long long cut_value;
-    unsigned q_count[3][kClasses];  // queue sizes by generation % 3 and class
-    unsigned q_grab[3];             // dynamic work counter of the block class
+    unsigned q_count[3][kClasses];  // queue sizes by generation % 3 and class (0, 1)
+    unsigned q_grab[3];             // dynamic work counter of the hub chunks
+    unsigned long long hub_pack[3]; // hub class: (count << 40) | total chunks
     int done;
+    unsigned trace_len;
 };
 
 struct GraphDev {
@@ -80,6 +84,14 @@ struct StateDev {
     unsigned char *dead;
     int *count;
     int *q[2][kClasses];
+    // per hub queue position (two generation sets): first chunk id, excess at
+    // compaction, excess not yet taken by a chunk, min key / min residual height,
+    // chunks finished
+    unsigned *hub_start[2];
+    long long *hub_e0[2];
+    long long *hub_rem[2];
+    unsigned long long *hub_aux[2];
+    unsigned *hub_done[2];
     Ctl *ctl;
     long long *bstats;          // [gridDim.x][kStatCount]
 };
@@ -102,11 +114,14 @@ struct Params {
     int cycle;
     int gap;
     int use_rev;
+    int multi_push;
     int small_max;
     int warp_max;
     long long max_iterations;
     unsigned long long timeout_ns;
     unsigned char *source_side;  // kModeCut output (device, n bytes) or null
+    unsigned long long *trace;   // optional: 4 words per grid barrier (where, gen, ns, queue total)
+    int trace_cap;               // records
 };
 
 // Launch helpers implemented in solver.cu.

@@ -99,7 +99,8 @@ def test_bipartite_matching(layout):
     assert got["value"] == hk
 
 
-def test_option_sweep_same_results():
+@pytest.mark.parametrize("multi_push", [1, 0])
+def test_option_sweep_same_results(multi_push):
     m = wb()
     g = W.rmat(12, 16, 5)
     src, dst, cap = g.numpy()
@@ -109,8 +110,24 @@ def test_option_sweep_same_results():
                                                    (8, 0, 0, 1, 7, 3), (8, 8, 2048, 1, 64, 1)]:
             o = m.wbpr_default_options()
             o.small_tile, o.small_max_degree, o.warp_max_degree = tile, smax, wmax
-            o.gap, o.cycle, o.grid_blocks = gap, cycle, grid
+            o.gap, o.cycle, o.grid_blocks, o.multi_push = gap, cycle, grid, multi_push
             check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o, ref=ref)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_single_push_mode_small_graphs(layout):
+    """The one-push-per-iteration rule of Alg. 1/2 gives the same results."""
+    m = wb()
+    o = m.wbpr_default_options()
+    o.multi_push = 0
+    for seed in range(60):
+        n = 2 + seed % 14
+        inst = W.random_small(n, (seed * 5) % 48, 8000 + seed, cap_lo=0, cap_hi=9)
+        src, dst, cap = inst.numpy()
+        bv, bs = oracle.mincut_brute(n, src, dst, cap, inst.s, inst.t)
+        got = gpu_solve(n, src, dst, cap, inst.s, inst.t, layout, o)
+        assert got["value"] == bv and np.array_equal(got["side"], bs), seed
+        assert oracle.verify_flow(n, src, dst, cap, inst.s, inst.t, got["flow"], bv)[0] == 0
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
