@@ -253,6 +253,44 @@ enum {
 wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg);
 wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64_t count);
 
+/*
+ * wbpr_maxflow_bcsr_noalloc -- maximum flow value of a small graph that the
+ * caller already holds in the BCSR layout, without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run -- code inside a host framework's
+ * execution phase that forbids allocation (a plugin's enqueue step, say),
+ * real-time loops whose device memory budget is fixed up front, or embedders
+ * that own no CUDA allocator.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine: the solver's working set (residual capacities, excesses,
+ * heights, queues, control block) lives in one fixed device array of about
+ * 11 MiB that every GPU loading the library holds until the process exits.
+ *   n, slots   vertex count (2 .. WBPR_NOALLOC_MAX_VERTICES) and BCSR entry
+ *              count (0 .. WBPR_NOALLOC_MAX_SLOTS); larger graphs are rejected
+ *              with WBPR_EINVAL.
+ *   s, t       source and sink.
+ *   off, col, cap, rev  device arrays of the BCSR layout (as wbpr_export
+ *              returns them for WBPR_ARRAY_OFFSETS, _COL, _CAP, _REV): int64
+ *              row offsets [n+1], int32 neighbour ids [slots] sorted within
+ *              each row, int32 initial residual capacities [slots], uint32
+ *              paired slot of each entry [slots].  Read only.
+ *   d_value    device int64: receives the maximum flow value.
+ *   d_residual NULL, or device int32[slots]: receives the residual capacity
+ *              of every slot at the end of the solve (cap - residual is the
+ *              flow of a maximum preflow).
+ * Synchronises `stream` and returns the solve's status.  The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array, which keeps the last call's contents (the call
+ * clears what must start at zero), so calls that overlap on the GPU -- from
+ * two host threads or two streams -- race and must not be issued.
+ */
+#define WBPR_NOALLOC_MAX_VERTICES 65536
+#define WBPR_NOALLOC_MAX_SLOTS 1048576
+wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32_t s, int32_t t,
+                                      const int64_t *off, const int32_t *col, const int32_t *cap,
+                                      const uint32_t *rev, wbpr_stream_t stream, int64_t *d_value,
+                                      int32_t *d_residual);
+
 #ifdef __cplusplus
 }
 #endif

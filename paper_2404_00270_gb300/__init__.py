@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "wbpr_mincut", "wbpr_maxflow_batch", "wbpr_destroy", "wbpr_default_options",
     "wbpr_get_options", "wbpr_set_options", "wbpr_get_stats", "wbpr_get_info",
     "wbpr_last_error", "wbpr_last_error_message", "wbpr_error_string", "wbpr_set_allocator",
-    "wbpr_run_stage", "wbpr_export",
+    "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc",
 ]
 
 
@@ -136,10 +136,11 @@ def load(build_if_missing: bool = False):
         lib.wbpr_set_allocator.argtypes = [_P, _P, _P]
         lib.wbpr_run_stage.argtypes = [_P, _P, i32, i64]
         lib.wbpr_export.argtypes = [_P, i32, _P, i64]
+        lib.wbpr_maxflow_bcsr_noalloc.argtypes = [i32, i64, i32, i32, _P, _P, _P, _P, _P, _P, _P]
         for name in ("wbpr_maxflow", "wbpr_maxflow_async", "wbpr_solve_status", "wbpr_mincut",
                      "wbpr_maxflow_batch", "wbpr_get_options", "wbpr_set_options",
                      "wbpr_get_stats", "wbpr_get_info", "wbpr_last_error", "wbpr_set_allocator",
-                     "wbpr_run_stage", "wbpr_export"):
+                     "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
         return lib
@@ -343,3 +344,20 @@ def wbpr_export(g: Graph, what: str, count: int | None = None) -> np.ndarray:
     out = np.zeros(count, dtype=dt)
     _check(load().wbpr_export(g.handle, code, out.ctypes.data if count else None, int(count)))
     return out
+
+
+NOALLOC_MAX_VERTICES = 65536
+NOALLOC_MAX_SLOTS = 1048576
+
+
+def wbpr_maxflow_bcsr_noalloc(n, slots, s, t, off, col, cap, rev, stream=None, d_value=None,
+                              d_residual=None) -> None:
+    """Allocation-free solve of a BCSR graph held in device tensors (see wbpr.h).
+
+    off int64[n+1], col int32[slots], cap int32[slots], rev int32[slots] (the
+    uint32 reverse slots viewed as int32), d_value int64[1] and optional
+    d_residual int32[slots], all on the current CUDA device."""
+    bo, bc, bk = _Buf(off, np.int64), _Buf(col, np.int32), _Buf(cap, np.int32)
+    br, bv, bres = _Buf(rev, np.int32), _Buf(d_value, np.int64), _Buf(d_residual, np.int32)
+    _check(load().wbpr_maxflow_bcsr_noalloc(int(n), int(slots), int(s), int(t), bo.ptr, bc.ptr, bk.ptr,
+                                            br.ptr, _stream(stream), bv.ptr, bres.ptr))
