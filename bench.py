@@ -53,6 +53,26 @@ def algorithmic_bytes(st: dict, n: int) -> int:
             B_GR_VERTEX * n * st["global_relabels"])
 
 
+def profiled_traffic():
+    """DRAM bytes (read + write) of one solve launch from the committed ncu
+    summary, or None when solver.cu changed since that capture."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "solve_kernel_rmat20.md")) as f:
+            text = f.read()
+        with open(os.path.join(ROOT, "paper_2404_00270_gb300", "csrc", "solver.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        tag = re.search(r"sha256 prefix `([0-9a-f]+)`", text).group(1)
+        if not sha.startswith(tag):
+            return None
+        rd = int(re.search(r"dram__bytes_read\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
+        wr = int(re.search(r"dram__bytes_write\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
+        return rd + wr
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -300,14 +320,7 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     launch_ms = solve_ms / args.steps
     achieved = (alg_bytes / args.steps) / (launch_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                traffic = json.load(f).get("traffic_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic() if args.scale == 20 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -337,7 +350,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wbpr", choices=["wbpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

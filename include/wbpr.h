@@ -73,7 +73,7 @@ typedef struct wbpr_options {
     int32_t small_tile;       /* 4, 8 or 16 lanes (default 8) */
     int32_t warp_max_degree;  /* longer rows (up to this) get one warp; longer
                                  rows (hubs) are split into chunks of 2048 entries
-                                 that whole thread blocks take (default 256) */
+                                 that whole thread blocks take (default 1024) */
     int32_t grid_blocks;      /* persistent grid size; 0 = automatic.  Clamped to
                                  the number of co-resident blocks. */
     int32_t barrier_timeout_ms; /* device wait limit (default 20000) */

@@ -15,7 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-OUT = os.path.join(HERE, "_build")
+# WBPR_BUILD_DIR / WBPR_NVCC_FLAGS let a tuning run build a variant of the
+# library next to the default one (e.g. -DWBPR_MIN_BLOCKS=4).
+OUT = os.environ.get("WBPR_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwbpr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -40,7 +42,8 @@ def up_to_date() -> bool:
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", src,
-           "-o", obj, "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+           "-o", obj, "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr",
+           *os.environ.get("WBPR_NVCC_FLAGS", "").split()]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -85,7 +85,7 @@ void wbpr_default_options(wbpr_options *o)
     o->cycle = 0;
     o->small_max_degree = 8;
     o->small_tile = 8;
-    o->warp_max_degree = 256;
+    o->warp_max_degree = 1024;
     o->grid_blocks = 0;
     o->barrier_timeout_ms = 20000;
     o->max_iterations = (int64_t)1 << 40;
@@ -333,7 +333,7 @@ namespace wbpr {
 static int auto_cycle(const wbpr_graph *g)
 {
     (void)g;
-    return 64;
+    return 16;
 }
 
 static int choose_grid(wbpr_graph *g)

@@ -576,25 +576,51 @@ __device__ __forceinline__ void mp_list(Ctx &c, int u, long long b, long long e,
                                         int sl, int hu, long long &rem, int &hres, int &npush,
                                         long long &scanned)
 {
+    // Groups of kIlp rounds: all loads of a group are issued before the
+    // (sequential) prefix-sum steps, so kIlp memory chains are in flight.
+    constexpr int kIlp = 4;
     const Params &P = c.P;
-    for (int r = 0; r < rounds; ++r) {
+    const GraphDev &g = P.g;
+    for (int r0 = 0; r0 < rounds; r0 += kIlp) {
         if (__all_sync(kFull, rem == 0)) break;
-        const long long base = b + (long long)r * W;
-        const long long k = base + sl;
-        int cap = 0, v = 0, hv = 0x7fffffff;
-        if (rem > 0 && k < e) mp_load<L>(P, k, in, cap, v, hv);
-        if (rem > 0 && base < e) scanned += (e - base < W) ? (e - base) : W;
-        long long amt = (cap > 0 && hv < hu && rem > 0) ? (long long)cap : 0;
-        long long incl = seg_incl_scan<W>(amt, sl);
-        long long tot = __shfl_sync(kFull, incl, W - 1, W);
-        long long d = rem - (incl - amt);
-        d = d < 0 ? 0 : (d > amt ? amt : d);
-        if (d > 0) {
-            mp_push<L>(P, u, k, in, v, (int)d);
-            ++npush;
+        int cap[kIlp], v[kIlp], hv[kIlp];
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            const long long base = b + (long long)(r0 + q) * W;
+            const long long k = base + sl;
+            cap[q] = 0;
+            v[q] = 0;
+            hv[q] = 0x7fffffff;
+            if (rem > 0 && r0 + q < rounds && k < e) {
+                if (L == kRCSR && in) {
+                    const unsigned j = __ldg(g.flow_idx + k);
+                    cap[q] = __ldcg(g.bf + j);
+                    v[q] = __ldg(g.in_col + k);
+                } else {
+                    cap[q] = __ldcg(g.cf + k);
+                    v[q] = __ldg(g.col + k);
+                }
+            }
+            if (rem > 0 && r0 + q < rounds && base < e) scanned += (e - base < W) ? (e - base) : W;
         }
-        if ((long long)cap - d > 0 && hv < hres) hres = hv;
-        rem -= tot < rem ? tot : rem;
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q)
+            if (cap[q] > 0) hv[q] = __ldcg(P.st.h + v[q]);
+#pragma unroll
+        for (int q = 0; q < kIlp; ++q) {
+            const long long k = b + (long long)(r0 + q) * W + sl;
+            long long amt = (cap[q] > 0 && hv[q] < hu && rem > 0) ? (long long)cap[q] : 0;
+            long long incl = seg_incl_scan<W>(amt, sl);
+            long long tot = __shfl_sync(kFull, incl, W - 1, W);
+            long long d = rem - (incl - amt);
+            d = d < 0 ? 0 : (d > amt ? amt : d);
+            if (d > 0) {
+                mp_push<L>(P, u, k, in, v[q], (int)d);
+                ++npush;
+            }
+            if ((long long)cap[q] - d > 0 && hv[q] < hres) hres = hv[q];
+            rem -= tot < rem ? tot : rem;
+        }
     }
 }
 
@@ -685,6 +711,15 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
     const long long r0 = (long long)j * kChunk;
     const long long r1 = deg < r0 + kChunk ? deg : r0 + kChunk;
     const int hu = __ldcg(P.st.h + u);
+    // Multi-push: once earlier chunks have taken all of the hub's excess this
+    // chunk has nothing to push and (no excess left) no relabel to inform.
+    bool spent = false;
+    if (P.multi_push) {
+        if (threadIdx.x == 0) c.sm.bcast64 = __ldcg(P.st.hub_rem[set] + pos);
+        __syncthreads();
+        spent = c.sm.bcast64 == 0;
+        __syncthreads();
+    }
     int capv[kPer], vv[kPer], hvv[kPer];
     long long asum = 0;
     u64 best = kNoKey;
@@ -694,7 +729,7 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
         capv[i] = 0;
         vv[i] = 0;
         hvv[i] = 0x7fffffff;
-        if (r < r1) {
+        if (r < r1 && !spent) {
             bool in;
             const long long k = row_slot<L>(ob, dout, ib, r, in);
             mp_load<L>(P, k, in, capv[i], vv[i], hvv[i]);
@@ -704,7 +739,7 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
             }
         }
     }
-    if (threadIdx.x == 0 && r1 > r0)
+    if (threadIdx.x == 0 && r1 > r0 && !spent)
         atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)(r1 - r0));
     if (!P.multi_push) {
         best = block_min(c, best);
@@ -924,20 +959,80 @@ __device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int 
     }
 }
 
+// Where the residual capacity that decides a BFS step over entry k of w's
+// list lives, and the neighbour v.  Backward: the arc v -> w; forward: w -> v.
+template <int L, int DIR>
+__device__ __forceinline__ const int *bfs_res_ptr(const Params &P, long long k, bool in, int w, int &v)
+{
+    const GraphDev &g = P.g;
+    if (L == kBCSR) {
+        v = __ldg(g.col + k);
+        if (DIR == kBfsForward) return g.cf + k;
+        if (P.use_rev) return g.cf + __ldg(g.rev + k);
+        return g.cf + lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), w);
+    }
+    if (!in) {  // out slot k of w: arc w -> v
+        v = __ldg(g.col + k);
+        return DIR == kBfsForward ? g.cf + k : g.bf + k;
+    }
+    v = __ldg(g.in_col + k);  // in slot of w: arc v -> w is out slot j
+    const unsigned j = __ldg(g.flow_idx + k);
+    return DIR == kBfsForward ? g.bf + j : g.cf + j;
+}
+
+// Visit up to NB entries at once: every load of a stage is issued before the
+// next stage (address, residual, visited mark), then the claims.
+template <int L, int DIR, int NB>
+__device__ __forceinline__ void bfs_entries(Ctx &c, int w, const long long (&k)[NB], const bool (&in)[NB],
+                                            const bool (&ok)[NB], int val, int nset, int n3)
+{
+    const Params &P = c.P;
+    int v[NB];
+    const int *rp[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        v[q] = 0;
+        rp[q] = nullptr;
+        if (ok[q]) rp[q] = bfs_res_ptr<L, DIR>(P, k[q], in[q], w, v[q]);
+    }
+    bool res[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) res[q] = ok[q] && __ldcg(rp[q]) > 0;
+    bool open[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        open[q] = false;
+        if (res[q]) open[q] = DIR == kBfsBackward ? __ldcg(P.st.h + v[q]) == kUnvisited
+                                                  : __ldcg(P.st.count + v[q]) == 0;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+        if (open[q]) bfs_visit<L, DIR>(c, v[q], val, nset, n3);
+}
+
 // Scan frontier vertex w with `W` lanes starting at lane `sl`.
 template <int L, int DIR, int W>
 __device__ void bfs_row(Ctx &c, int w, int sl, int val, int nset, int n3)
 {
+    constexpr int NB = 4;
     const GraphDev &g = c.P.g;
-    long long ob = __ldg(g.off + w), oe = __ldg(g.off + w + 1);
-    for (long long k = ob + sl; k < oe; k += W) {
-        if (residual_to<L, DIR>(c.P, k, false, w)) bfs_visit<L, DIR>(c, __ldg(g.col + k), val, nset, n3);
-    }
+    const long long ob = __ldg(g.off + w), dout = __ldg(g.off + w + 1) - ob;
+    long long ib = 0, din = 0;
     if (L == kRCSR) {
-        long long ib = __ldg(g.in_off + w), ie = __ldg(g.in_off + w + 1);
-        for (long long k = ib + sl; k < ie; k += W) {
-            if (residual_to<L, DIR>(c.P, k, true, w)) bfs_visit<L, DIR>(c, __ldg(g.in_col + k), val, nset, n3);
+        ib = __ldg(g.in_off + w);
+        din = __ldg(g.in_off + w + 1) - ib;
+    }
+    const long long deg = dout + din;
+    for (long long r0 = sl; r0 < deg; r0 += (long long)NB * W) {
+        long long k[NB];
+        bool in[NB], ok[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const long long r = r0 + (long long)q * W;
+            ok[q] = r < deg;
+            k[q] = row_slot<L>(ob, dout, ib, ok[q] ? r : 0, in[q]);
         }
+        bfs_entries<L, DIR, NB>(c, w, k, in, ok, val, nset, n3);
     }
 }
 
@@ -945,6 +1040,7 @@ __device__ void bfs_row(Ctx &c, int w, int sl, int val, int nset, int n3)
 template <int L, int DIR>
 __device__ long long bfs_chunk(Ctx &c, int set, unsigned pos, unsigned j, int val, int nset, int n3)
 {
+    constexpr int NB = kChunk / kBlock;
     const GraphDev &g = c.P.g;
     const int w = __ldcg(c.P.st.q[set][2] + pos);
     const long long ob = __ldg(g.off + w), dout = __ldg(g.off + w + 1) - ob;
@@ -956,12 +1052,15 @@ __device__ long long bfs_chunk(Ctx &c, int set, unsigned pos, unsigned j, int va
     const long long deg = dout + din;
     const long long r0 = (long long)j * kChunk;
     const long long r1 = deg < r0 + kChunk ? deg : r0 + kChunk;
-    for (long long r = r0 + threadIdx.x; r < r1; r += kBlock) {
-        bool in;
-        const long long k = row_slot<L>(ob, dout, ib, r, in);
-        if (residual_to<L, DIR>(c.P, k, in, w))
-            bfs_visit<L, DIR>(c, in ? __ldg(g.in_col + k) : __ldg(g.col + k), val, nset, n3);
+    long long k[NB];
+    bool in[NB], ok[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const long long r = r0 + threadIdx.x + (long long)q * kBlock;
+        ok[q] = r < r1;
+        k[q] = row_slot<L>(ob, dout, ib, ok[q] ? r : 0, in[q]);
     }
+    bfs_entries<L, DIR, NB>(c, w, k, in, ok, val, nset, n3);
     return r1 > r0 ? r1 - r0 : 0;
 }
 
@@ -1228,8 +1327,14 @@ __device__ bool min_cut(Ctx &c)
     return grid_sync(c, 32);
 }
 
+// At least WBPR_MIN_BLOCKS resident blocks per SM: the solver is bound by
+// memory latency, so occupancy (more warps in flight) matters more than the
+// few registers it costs.
+#ifndef WBPR_MIN_BLOCKS
+#define WBPR_MIN_BLOCKS 4
+#endif
 template <int L, int SW>
-__global__ void __launch_bounds__(kBlock) solve_kernel(Params P)
+__global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) solve_kernel(Params P)
 {
     __shared__ Smem sm;
     Ctx c{P, sm, 0ull, 0};
