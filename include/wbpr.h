@@ -82,7 +82,16 @@ typedef struct wbpr_options {
     int32_t trace;            /* > 0: record up to this many grid barriers of each
                                  solve (barrier id, queue generation, device time in ns,
                                  queue sizes); read with wbpr_export(WBPR_ARRAY_TRACE) */
-    int32_t reserved;
+    float gr_ratio;           /* > 0: start a global relabel once the push-relabel
+                                 iterations since the last one took gr_ratio times
+                                 as long as it did (default 1.0); `cycle` then only
+                                 caps the iterations in between.  0 = every `cycle`
+                                 iterations */
+    int32_t batch_team;       /* wbpr_maxflow_batch: blocks that solve one large
+                                 instance together (power of two, default 16) */
+    int64_t batch_big_slots;  /* wbpr_maxflow_batch: instances with more residual
+                                 slots than this are large (default 2^20); smaller
+                                 ones are solved by a single block each */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */
@@ -263,7 +272,7 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
  * that own no CUDA allocator.  It calls no cudaMalloc, cudaFree or allocating
  * library routine: the solver's working set (residual capacities, excesses,
  * heights, queues, control block) lives in one fixed device array of about
- * 11 MiB that every GPU loading the library holds until the process exits.
+ * 15 MiB that every GPU loading the library holds until the process exits.
  *   n, slots   vertex count (2 .. WBPR_NOALLOC_MAX_VERTICES) and BCSR entry
  *              count (0 .. WBPR_NOALLOC_MAX_SLOTS); larger graphs are rejected
  *              with WBPR_EINVAL.

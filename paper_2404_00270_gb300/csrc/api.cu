@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "handle.h"
 #include "wbpr.h"
@@ -89,6 +90,10 @@ void wbpr_default_options(wbpr_options *o)
     o->grid_blocks = 0;
     o->barrier_timeout_ms = 20000;
     o->max_iterations = (int64_t)1 << 40;
+    o->trace = 0;
+    o->gr_ratio = 1.0f;
+    o->batch_team = 16;
+    o->batch_big_slots = (int64_t)1 << 20;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -129,6 +134,9 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->small_max_degree < 0 || o->warp_max_degree < o->small_max_degree) return WBPR_EINVAL;
     if (o->grid_blocks < 0 || o->barrier_timeout_ms <= 0 || o->max_iterations <= 0) return WBPR_EINVAL;
     if (o->trace < 0 || o->trace > (1 << 24)) return WBPR_EINVAL;
+    if (!(o->gr_ratio >= 0.f && o->gr_ratio < 1e6f)) return WBPR_EINVAL;
+    if (o->batch_team < 1 || o->batch_team > 64 || (o->batch_team & (o->batch_team - 1))) return WBPR_EINVAL;
+    if (o->batch_big_slots < 0) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -332,8 +340,8 @@ namespace wbpr {
 
 static int auto_cycle(const wbpr_graph *g)
 {
-    (void)g;
-    return 16;
+    // With the time-balanced trigger the cycle is only a cap.
+    return g->opts.gr_ratio > 0.f ? 1000 : 16;
 }
 
 static int choose_grid(wbpr_graph *g)
@@ -370,6 +378,7 @@ static Params make_params(wbpr_graph *g, int mode)
     p.g.cf = g->cf;
     p.g.cf0 = g->cf0;
     p.g.rev = g->rev;
+    p.g.cfb = (g->layout == WBPR_BCSR && g->opts.use_rev) ? g->cfb : nullptr;
     p.g.bf = g->bf;
     p.g.in_off = g->in_off;
     p.g.in_col = g->in_col;
@@ -391,6 +400,8 @@ static Params make_params(wbpr_graph *g, int mode)
     p.mode = mode;
     p.cycle = g->opts.cycle > 0 ? g->opts.cycle : auto_cycle(g);
     p.gap = g->opts.gap;
+    p.gr_ratio = g->opts.gr_ratio;
+    p.g.layout_tag = g->layout == WBPR_BCSR ? kBCSR : kRCSR;
     p.multi_push = g->opts.multi_push;
     p.use_rev = g->layout == WBPR_BCSR ? g->opts.use_rev : 0;
     p.small_max = g->opts.small_max_degree;
@@ -417,7 +428,10 @@ static wbpr_status launch_solver(wbpr_graph *g, cudaStream_t st, int mode, long 
     Params p = make_params(g, mode);
     p.iters_arg = iters;
     p.source_side = side;
-    if (mode & kModeIters) p.gap = 0;
+    if (mode & kModeIters) {
+        p.gap = 0;
+        p.gr_ratio = 0.f;
+    }
     API_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st));
     API_CUDA(cudaMemsetAsync(g->bstats, 0, sizeof(long long) * (size_t)grid * kStatCount, st));
     API_CUDA(cudaEventRecord(g->ev0, st));
@@ -573,16 +587,118 @@ wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream
 {
     if (count < 0 || (count > 0 && (!gs || !values)))
         return set_error(WBPR_EINVAL, "wbpr_maxflow_batch: bad arguments");
+    int device = 0;
+    if (count > 0 && cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WBPR_ECUDA, "wbpr_maxflow_batch: no CUDA device");
+    }
     for (int i = 0; i < count; ++i) {
         if (!gs[i]) return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: NULL handle");
-        for (int j = 0; j < i; ++j)
-            if (gs[j] == gs[i]) return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: repeated handle");
+        if (gs[i]->device != device) return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: handle of another device");
     }
+    {
+        std::vector<const wbpr_graph *> sorted(gs, gs + count);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: repeated handle");
+    }
+    if (count == 0) return WBPR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const wbpr_options &bo = gs[0]->opts;
+    const int num_sms = gs[0]->num_sms;
+    // groups: (layout, large?) -- large instances first, largest first within a group
+    std::vector<int> groups[2][2];
     for (int i = 0; i < count; ++i) {
-        wbpr_status rc = wbpr_maxflow(gs[i], stream, values + i, edge_flows ? edge_flows[i] : nullptr);
-        if (rc != WBPR_OK) return rc;
+        const int lay = gs[i]->layout == WBPR_BCSR ? 1 : 0;
+        const int big = gs[i]->slots > bo.batch_big_slots ? 1 : 0;
+        groups[lay][big].push_back(i);
     }
-    return WBPR_OK;
+    std::vector<BatchOut> outs((size_t)count);
+    for (int big = 1; big >= 0; --big) {
+        for (int lay = 0; lay < 2; ++lay) {
+            std::vector<int> &grp = groups[lay][big];
+            if (grp.empty()) continue;
+            std::stable_sort(grp.begin(), grp.end(), [&](int a, int b) { return gs[a]->slots > gs[b]->slots; });
+            const int team = big ? bo.batch_team : 1;
+            const int layout = lay ? kBCSR : kRCSR;
+            int per_sm = 0;
+            if (batch_max_blocks_per_sm(layout, &per_sm) != cudaSuccess || per_sm < 1) {
+                cudaGetLastError();
+                return set_error(WBPR_ECUDA, "wbpr_maxflow_batch: occupancy query failed");
+            }
+            long long teams = (long long)per_sm * num_sms / team;
+            if (teams > (long long)grp.size()) teams = (long long)grp.size();
+            if (teams < 1) teams = 1;
+            const int grid = (int)(teams * team);
+            const size_t n_items = grp.size();
+            std::vector<Params> hp(n_items);
+            for (size_t j = 0; j < n_items; ++j) {
+                wbpr_graph *g = gs[grp[j]];
+                const bool want_flow = edge_flows && edge_flows[grp[j]];
+                hp[j] = make_params(g, kModePreflow | kModePhase1 | (want_flow ? kModePhase2 : 0));
+                g->grid_blocks = team;
+            }
+            const size_t bytes_p = sizeof(Params) * n_items, bytes_o = sizeof(BatchOut) * n_items;
+            const size_t bytes_c = 256 + 16 * (size_t)teams;
+            Params *dp = (Params *)dev_alloc(bytes_p, st);
+            BatchOut *dout = (BatchOut *)dev_alloc(bytes_o, st);
+            unsigned char *dc = (unsigned char *)dev_alloc(bytes_c, st);
+            auto release = [&]() {
+                dev_free(dp, bytes_p, st);
+                dev_free(dout, bytes_o, st);
+                dev_free(dc, bytes_c, st);
+            };
+            if (!dp || !dout || !dc) {
+                release();
+                return set_error(WBPR_ENOMEM, "wbpr_maxflow_batch: device allocation failed");
+            }
+            BatchDesc b;
+            memset(&b, 0, sizeof(b));
+            b.params = dp;
+            b.count = (int)n_items;
+            b.team = team;
+            b.next = (unsigned *)dc;
+            b.team_bar = (unsigned long long *)(dc + 256);
+            b.team_item = (unsigned *)(dc + 256 + 8 * (size_t)teams);
+            b.out = dout;
+            b.timeout_ns = (unsigned long long)bo.barrier_timeout_ms * 1000000ull;
+            cudaError_t e = cudaMemcpyAsync(dp, hp.data(), bytes_p, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, bytes_c, st);
+            if (e == cudaSuccess) e = batch_launch(layout, grid, b, st);
+            std::vector<BatchOut> ho(n_items);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ho.data(), dout, bytes_o, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            release();
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(WBPR_ECUDA, std::string("wbpr_maxflow_batch: ") + cudaGetErrorString(e));
+            }
+            for (size_t j = 0; j < n_items; ++j) outs[(size_t)grp[j]] = ho[j];
+        }
+    }
+    wbpr_status rc = WBPR_OK;
+    for (int i = 0; i < count; ++i) {
+        wbpr_graph *g = gs[i];
+        const BatchOut &o = outs[(size_t)i];
+        memset(&g->stats, 0, sizeof(g->stats));
+        g->stats.iterations = o.iterations;
+        g->stats.solve_ms = (double)o.ns * 1e-6;
+        if (o.err != 0) {
+            g->solved_flow = g->solved_value = false;
+            if (rc == WBPR_OK)
+                rc = set_error((wbpr_status)o.err, "wbpr_maxflow_batch: instance " + std::to_string(i) + " gave up");
+            continue;
+        }
+        values[i] = o.value;
+        const bool want_flow = edge_flows && edge_flows[i];
+        g->solved_value = true;
+        g->solved_flow = want_flow;
+        if (want_flow)
+            API_CUDA(launch_edge_flow(g->layout, g->m, g->arc2slot, g->cf0, g->cf, g->bf, g->prefix, g->cap_in,
+                                      edge_flows[i], st));
+    }
+    API_CUDA(cudaStreamSynchronize(st));
+    return rc;
 }
 
 wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg)
@@ -605,7 +721,10 @@ wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, i
     g->grid_blocks = grid;
     Params p = make_params(g, mode);
     p.iters_arg = arg;
-    if (mode & kModeIters) p.gap = 0;
+    if (mode & kModeIters) {
+        p.gap = 0;
+        p.gr_ratio = 0.f;
+    }
     long long keep[3] = {0, 0, 0};
     if (mode != kModePreflow) {
         Ctl c;

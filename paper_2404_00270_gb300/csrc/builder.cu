@@ -41,7 +41,10 @@ __global__ void validate_keys(long long m, int n, const int *src, const int *dst
         }
         val[i] = (unsigned)i;
     }
-    if (local) atomicAdd(nonloop, local);
+    typedef cub::BlockReduce<unsigned long long, 256> Reduce;
+    __shared__ typename Reduce::TempStorage tmp;
+    local = Reduce(tmp).Sum(local);
+    if (threadIdx.x == 0 && local) atomicAdd(nonloop, local);
 }
 
 __global__ void gather_caps(long long mp, const unsigned *val, const int *cap, int *out)
@@ -162,7 +165,10 @@ __global__ void max_degree_kernel(int n, const long long *off, const long long *
         if (in_off) d += in_off[v + 1] - in_off[v];
         if ((unsigned long long)d > mx) mx = (unsigned long long)d;
     }
-    atomicMax(out, mx);
+    typedef cub::BlockReduce<unsigned long long, 256> Reduce;
+    __shared__ typename Reduce::TempStorage tmp;
+    mx = Reduce(tmp).Reduce(mx, cuda::maximum<>());
+    if (threadIdx.x == 0 && mx) atomicMax(out, mx);
 }
 
 __global__ void arc_slots_bcsr(long long m, const int *src, const int *dst, const int *col,
@@ -401,6 +407,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         OWN_ALLOC(g->cf, int, S);
         OWN_ALLOC(g->cf0, int, S);
         OWN_ALLOC(g->rev, unsigned, S);
+        OWN_ALLOC(g->cfb, int, S);
         if (S > 0) {
             BUILD_CUDA(cudaMemsetAsync(csum, 0, sizeof(long long) * S, st));
             merge_runs<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, heads, ukey, g->col, csum);

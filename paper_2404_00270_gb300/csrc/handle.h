@@ -42,6 +42,7 @@ struct wbpr_graph {
     int *cf = nullptr;
     int *cf0 = nullptr;
     unsigned *rev = nullptr;
+    int *cfb = nullptr;       // BCSR: mirrored reverse residual
     int *bf = nullptr;
     long long *in_off = nullptr;
     int *in_col = nullptr;

@@ -29,7 +29,8 @@ constexpr int kMaxGrid = 1024;
 // Scratch layout (byte offsets, each 256-aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffCf = 0;
-constexpr size_t kOffE = align256(kOffCf + 4 * kMaxSlots);
+constexpr size_t kOffCfb = align256(kOffCf + 4 * kMaxSlots);
+constexpr size_t kOffE = align256(kOffCfb + 4 * kMaxSlots);
 constexpr size_t kOffH = align256(kOffE + 8 * kMaxN);
 constexpr size_t kOffDead = align256(kOffH + 4 * kMaxN);
 constexpr size_t kOffCount = align256(kOffDead + kMaxN);
@@ -122,6 +123,7 @@ extern "C" wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32
     p.g.cf = (int *)(base + kOffCf);
     p.g.cf0 = cap;
     p.g.rev = rev;
+    p.g.cfb = (int *)(base + kOffCfb);
     p.st.e = (long long *)(base + kOffE);
     p.st.h = (int *)(base + kOffH);
     p.st.dead = base + kOffDead;

@@ -93,11 +93,17 @@ struct Smem {
     int ok;
 };
 
+// Per-block view of one solve.  A solve runs on a team of `nblk` blocks:
+// the whole grid for a single instance, or a slice of it in a batch; `bid`
+// is this block's rank in the team.
 struct Ctx {
     const Params &P;
     Smem &sm;
     u64 bar_target;  // meaningful in thread 0 only
-    int gen;         // queue generation (uniform across the grid)
+    int gen;         // queue generation (uniform across the team)
+    unsigned nblk;
+    unsigned bid;
+    u64 gr_start_ns, gr_ns, gr_end_ns;  // last global relabel (rank 0, thread 0)
 };
 
 // Grid-wide barrier with a time limit.  Returns false on any device error.
@@ -106,13 +112,13 @@ __device__ bool grid_sync(Ctx &c, int where)
     __syncthreads();
     if (threadIdx.x == 0) {
         Ctl *ctl = c.P.st.ctl;
-        c.bar_target += gridDim.x;
+        c.bar_target += c.nblk;
         __threadfence();
-        if (gridDim.x > 1) atomicAdd(&ctl->bar, 1ULL);
+        if (c.nblk > 1) atomicAdd(&ctl->bar, 1ULL);
         int ok = 1;
         u64 t0 = 0;
         unsigned spins = 0;
-        while (gridDim.x > 1 && ld_acquire(&ctl->bar) < c.bar_target) {
+        while (c.nblk > 1 && ld_acquire(&ctl->bar) < c.bar_target) {
             if (ld_err(ctl) != 0) { ok = 0; break; }
             ++spins;
             if ((spins & 255u) == 0) {
@@ -131,7 +137,7 @@ __device__ bool grid_sync(Ctx &c, int where)
         __threadfence();
         if (ld_err(ctl) != 0) ok = 0;
         c.sm.ok = ok;
-        if (c.P.trace && blockIdx.x == 0) {
+        if (c.P.trace && c.bid == 0) {
             unsigned i = ctl->trace_len;
             if (i < (unsigned)c.P.trace_cap) {
                 const unsigned *q = ctl->q_count[c.gen % 3];
@@ -200,7 +206,7 @@ __device__ void q_flush(Ctx &c, int slot3, int set)
 
 __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (c.bid == 0 && threadIdx.x == 0) {
         Ctl *ctl = c.P.st.ctl;
         int z = (gen + 2) % 3;
         for (int k = 0; k < kClasses; ++k) ctl->q_count[z][k] = 0;
@@ -415,6 +421,7 @@ __device__ void apply_op(Ctx &c, int u, u64 key, bool phase1, int hcap)
             int v;
             int *dec;
             int *inc;
+            long long mir_a = -1, mir_ra = -1;
             if (L == kBCSR) {
                 long long a = __ldg(g.off + u) + idx;
                 v = __ldg(g.col + a);
@@ -426,6 +433,8 @@ __device__ void apply_op(Ctx &c, int u, u64 key, bool phase1, int hcap)
                 }
                 dec = g.cf + a;
                 inc = g.cf + ra;
+                mir_a = a;
+                mir_ra = ra;
             } else {
                 long long ob = __ldg(g.off + u);
                 unsigned dout = (unsigned)(__ldg(g.off + u + 1) - ob);
@@ -448,6 +457,10 @@ __device__ void apply_op(Ctx &c, int u, u64 key, bool phase1, int hcap)
                 atomicSub(dec, (int)d);
                 atomicAdd((u64 *)(e + u), (u64)(-d));
                 atomicAdd(inc, (int)d);
+                if (L == kBCSR && g.cfb) {
+                    atomicAdd(g.cfb + mir_a, (int)d);
+                    atomicSub(g.cfb + mir_ra, (int)d);
+                }
                 atomicAdd((u64 *)(e + v), (u64)d);
                 atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], 1ull);
             }
@@ -558,6 +571,10 @@ __device__ __forceinline__ void mp_push(const Params &P, int u, long long k, boo
                                  : lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), u);
         dec = g.cf + k;
         inc = g.cf + ra;
+        if (g.cfb) {
+            atomicAdd(g.cfb + k, d);
+            atomicSub(g.cfb + ra, d);
+        }
     } else if (!in) {
         dec = g.cf + k;
         inc = g.bf + k;
@@ -829,8 +846,8 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
             while (grab_chunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_chunk<L>(c, set, pos, j, nch, phase1, hcap);
     }
     const int lane = threadIdx.x & 31;
-    const unsigned gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const unsigned nwarps = gridDim.x * kWarps;
+    const unsigned gwarp = c.bid * kWarps + (threadIdx.x >> 5);
+    const unsigned nwarps = c.nblk * kWarps;
     {
         const int *q1 = P.st.q[set][1];
         for (unsigned i = gwarp; i < c1; i += nwarps) {
@@ -869,8 +886,8 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
         int cand = __ldcg(&P.st.ctl->gap_level[(gen + 2) % 3]);
         if (cand < n && __ldcg(P.st.count + cand) == 0) gap = cand;
     }
-    const long long chunk = ((long long)n + gridDim.x - 1) / gridDim.x;
-    const long long v0 = chunk * blockIdx.x;
+    const long long chunk = ((long long)n + c.nblk - 1) / c.nblk;
+    const long long v0 = chunk * c.bid;
     const long long v1 = v0 + chunk < n ? v0 + chunk : n;
     long long nact = 0, lifted = 0;
     for (long long base = v0; base < v1; base += kBlock) {
@@ -901,7 +918,7 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
     }
     q_flush(c, s3, set);
     if (nact) atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)nact);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && gap != kUnvisited)
+    if (c.bid == 0 && threadIdx.x == 0 && gap != kUnvisited)
         atomicAdd((unsigned long long *)&c.sm.stats[kStatGaps], 1ull);
     (void)lifted;
 }
@@ -922,6 +939,7 @@ __device__ __forceinline__ bool residual_to(const Params &P, long long slot, boo
     const GraphDev &g = P.g;
     if (L == kBCSR) {
         if (DIR == kBfsForward) return __ldcg(g.cf + slot) > 0;
+        if (g.cfb) return __ldcg(g.cfb + slot) > 0;
         long long ra;
         if (P.use_rev) {
             ra = __ldg(g.rev + slot);
@@ -968,6 +986,7 @@ __device__ __forceinline__ const int *bfs_res_ptr(const Params &P, long long k, 
     if (L == kBCSR) {
         v = __ldg(g.col + k);
         if (DIR == kBfsForward) return g.cf + k;
+        if (g.cfb) return g.cfb + k;  // mirrored backward residual, read in place
         if (P.use_rev) return g.cf + __ldg(g.rev + k);
         return g.cf + lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), w);
     }
@@ -1091,8 +1110,8 @@ __device__ void bfs_level(Ctx &c, int val)
         }
     }
     const int lane = threadIdx.x & 31;
-    const unsigned gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const unsigned nwarps = gridDim.x * kWarps;
+    const unsigned gwarp = c.bid * kWarps + (threadIdx.x >> 5);
+    const unsigned nwarps = c.nblk * kWarps;
     {
         const int *q1 = P.st.q[set][1];
         for (unsigned i = gwarp; i < c1; i += nwarps) {
@@ -1103,8 +1122,8 @@ __device__ void bfs_level(Ctx &c, int val)
     }
     {
         const int *q0 = P.st.q[set][0];
-        const unsigned gt = (blockIdx.x * kBlock + threadIdx.x) / SW;
-        const unsigned ntiles = gridDim.x * kBlock / SW;
+        const unsigned gt = (c.bid * kBlock + threadIdx.x) / SW;
+        const unsigned ntiles = c.nblk * kBlock / SW;
         const int sl = threadIdx.x % SW;
         for (unsigned i = gt; i < c0; i += ntiles) {
             int w = __ldcg(q0 + i);
@@ -1120,7 +1139,7 @@ __device__ void bfs_level(Ctx &c, int val)
 template <int L>
 __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (c.bid == 0 && threadIdx.x == 0) {
         const long long d = degree<L>(c.P.g, v);
         const int cls = classify(c.P, d);
         c.P.st.q[gen & 1][cls][0] = v;
@@ -1148,8 +1167,9 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
     const int base = phase1 ? 0 : n;
     const int unreach = phase1 ? n : 2 * n;
     const bool gap = phase1 && P.gap;
-    const long long stride = (long long)gridDim.x * kBlock;
-    for (long long v = blockIdx.x * kBlock + threadIdx.x; v <= n; v += stride) {
+    if (c.bid == 0 && threadIdx.x == 0) c.gr_start_ns = global_ns();
+    const long long stride = (long long)c.nblk * kBlock;
+    for (long long v = c.bid * kBlock + threadIdx.x; v <= n; v += stride) {
         if (gap) __stcg(P.st.count + v, 0);
         if (v == n || v == excluded) continue;
         if (phase1 && P.st.dead[v]) continue;
@@ -1160,13 +1180,13 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
-        if (gap && blockIdx.x == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
+        if (gap && c.bid == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
         bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
         if (!grid_sync(c, 11)) return false;
         c.gen++;
     }
     long long wo = 0;
-    for (long long v = blockIdx.x * kBlock + threadIdx.x; v < n; v += stride) {
+    for (long long v = c.bid * kBlock + threadIdx.x; v < n; v += stride) {
         if (v == excluded) continue;
         if (__ldcg(P.st.h + v) == kUnvisited) {
             __stcg(P.st.h + v, unreach);
@@ -1181,8 +1201,13 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
         atomicAdd((u64 *)&P.st.ctl->excess_total, (u64)(-bw));
         atomicAdd((u64 *)&P.st.ctl->written_off, (u64)bw);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.st.ctl->global_relabels++;
-    return grid_sync(c, 12);
+    if (c.bid == 0 && threadIdx.x == 0) P.st.ctl->global_relabels++;
+    const bool ok = grid_sync(c, 12);
+    if (c.bid == 0 && threadIdx.x == 0) {
+        c.gr_end_ns = global_ns();
+        c.gr_ns = c.gr_end_ns - c.gr_start_ns;
+    }
+    return ok;
 }
 
 // `max_it` iterations of Alg. 2 (fewer if the AVQ empties).  Returns false
@@ -1193,6 +1218,11 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
     const Params &P = c.P;
     const int hcap = phase1 ? P.g.n : 2 * P.g.n;
     for (long long i = 0; i < max_it; ++i) {
+        // Time-balanced global relabel: once the iterations since the last
+        // global relabel have taken gr_ratio times as long as it did.
+        // The flag names the generation whose iteration raised it, so it never
+        // needs clearing (a clear could race with a slower block's read).
+        if (i > 0 && P.gr_ratio > 0.f && __ldcg(&P.st.ctl->gr_due_gen) == c.gen - 1) break;
         build_avq<L>(c, phase1, hcap);
         if (!grid_sync(c, 20)) return false;
         const unsigned tot = queue_total(P.st.ctl, c.gen);
@@ -1203,11 +1233,15 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
             break;
         }
         pr_process<L, SW>(c, phase1, hcap);
+        if (c.bid == 0 && threadIdx.x == 0 && P.gr_ratio > 0.f) {
+            const u64 now = global_ns();
+            if ((float)(now - c.gr_end_ns) >= P.gr_ratio * (float)c.gr_ns) P.st.ctl->gr_due_gen = c.gen;
+        }
         if (!grid_sync(c, 22)) return false;
         c.gen++;
         ++*it_total;
         if (*it_total >= P.max_iterations) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (c.bid == 0 && threadIdx.x == 0) {
                 atomicCAS(&P.st.ctl->err, 0, (int)WBPR_ETIMEOUT);
                 P.st.ctl->err_where = 23;
             }
@@ -1235,7 +1269,7 @@ __device__ bool run_phase(Ctx &c, bool phase1, long long *it_total)
         // instead of looping.
         idle_rounds = (*it_total == before) ? idle_rounds + 1 : 0;
         if (idle_rounds >= 2) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (c.bid == 0 && threadIdx.x == 0) {
                 atomicCAS(&ctl->err, 0, (int)WBPR_ESTATE);
                 ctl->err_where = 24;
             }
@@ -1252,11 +1286,12 @@ __device__ bool preflow(Ctx &c)
 {
     const Params &P = c.P;
     const GraphDev &g = P.g;
-    const long long stride = (long long)gridDim.x * kBlock;
-    const long long tid = blockIdx.x * kBlock + threadIdx.x;
+    const long long stride = (long long)c.nblk * kBlock;
+    const long long tid = c.bid * kBlock + threadIdx.x;
     for (long long k = tid; k < g.slots; k += stride) {
         g.cf[k] = __ldg(g.cf0 + k);
         if (L == kRCSR) g.bf[k] = 0;
+        if (L == kBCSR && g.cfb) g.cfb[k] = __ldg(g.cf0 + __ldg(g.rev + k));
     }
     for (long long v = tid; v < g.n; v += stride) {
         P.st.e[v] = 0;
@@ -1275,6 +1310,10 @@ __device__ bool preflow(Ctx &c)
             long long ra = P.use_rev ? (long long)__ldg(g.rev + k)
                                      : lower_bound_col(g.col, __ldg(g.off + v), __ldg(g.off + v + 1), g.s);
             atomicAdd(g.cf + ra, cap);
+            if (g.cfb) {
+                atomicAdd(g.cfb + k, cap);
+                atomicSub(g.cfb + ra, cap);
+            }
         } else {
             atomicAdd(g.bf + k, cap);
         }
@@ -1296,8 +1335,8 @@ __device__ bool min_cut(Ctx &c)
     const Params &P = c.P;
     const GraphDev &g = P.g;
     const int n = g.n;
-    const long long stride = (long long)gridDim.x * kBlock;
-    const long long tid = blockIdx.x * kBlock + threadIdx.x;
+    const long long stride = (long long)c.nblk * kBlock;
+    const long long tid = c.bid * kBlock + threadIdx.x;
     int *mark = P.st.count;
     for (long long v = tid; v <= n; v += stride) __stcg(mark + v, v == g.s ? 1 : 0);
     seed_queue<L>(c, c.gen, g.s);
@@ -1311,7 +1350,7 @@ __device__ bool min_cut(Ctx &c)
     }
     // cut capacity: arcs from the marked side to the rest (initial capacities)
     const int lane = threadIdx.x & 31;
-    const long long gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const long long gw = (c.bid * kBlock + threadIdx.x) >> 5;
     const long long nw = stride >> 5;
     long long sum = 0;
     for (long long u = gw; u < n; u += nw) {
@@ -1333,30 +1372,123 @@ __device__ bool min_cut(Ctx &c)
 #ifndef WBPR_MIN_BLOCKS
 #define WBPR_MIN_BLOCKS 4
 #endif
+
+// One whole solve (the modes in P.mode) by the calling team of blocks.
 template <int L, int SW>
-__global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) solve_kernel(Params P)
+__device__ void solve_instance(Ctx &c)
 {
-    __shared__ Smem sm;
-    Ctx c{P, sm, 0ull, 0};
+    const Params &P = c.P;
+    Smem &sm = c.sm;
     if (threadIdx.x < kClasses) sm.qcnt[threadIdx.x] = 0;
     if (threadIdx.x < kStatCount) sm.stats[threadIdx.x] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (c.bid == 0 && threadIdx.x == 0) {
         for (int k = 0; k < 3; ++k) P.st.ctl->gap_level[k] = kUnvisited;
+        P.st.ctl->gr_due_gen = -1;
+    }
     __syncthreads();
     long long it_total = 0;
     bool ok = true;
     if (P.mode & kModePreflow) ok = preflow<L>(c);
     if (ok && (P.mode & kModePhase1)) {
         ok = run_phase<L, SW>(c, true, &it_total);
-        if (blockIdx.x == 0 && threadIdx.x == 0) P.st.ctl->phase1_iterations = it_total;
+        if (c.bid == 0 && threadIdx.x == 0) P.st.ctl->phase1_iterations = it_total;
     }
     if (ok && (P.mode & kModeGrOnce)) ok = global_relabel<L, SW>(c, true);
     if (ok && (P.mode & kModeIters)) ok = iterate<L, SW>(c, true, P.iters_arg, &it_total);
     if (ok && (P.mode & kModePhase2)) ok = run_phase<L, SW>(c, false, &it_total);
     if (ok && (P.mode & kModeCut)) ok = min_cut<L, SW>(c);
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.st.ctl->iterations = it_total;
+    if (c.bid == 0 && threadIdx.x == 0) P.st.ctl->iterations = it_total;
     __syncthreads();
-    if (threadIdx.x < kStatCount) P.st.bstats[(long long)blockIdx.x * kStatCount + threadIdx.x] = sm.stats[threadIdx.x];
+    if (threadIdx.x < kStatCount) P.st.bstats[(long long)c.bid * kStatCount + threadIdx.x] = sm.stats[threadIdx.x];
+    __syncthreads();
+}
+
+template <int L, int SW>
+__global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) solve_kernel(Params P)
+{
+    __shared__ Smem sm;
+    Ctx c{P, sm, 0ull, 0, gridDim.x, blockIdx.x, 0ull, 0ull, 0ull};
+    solve_instance<L, SW>(c);
+}
+
+// Team barrier of the batch kernel (teams of more than one block).
+__device__ bool team_sync(const BatchDesc &B, unsigned team, u64 &target, Smem &sm)
+{
+    __syncthreads();
+    if (B.team > 1 && threadIdx.x == 0) {
+        target += B.team;
+        __threadfence();
+        atomicAdd(B.team_bar + team, 1ULL);
+        u64 t0 = 0;
+        unsigned spins = 0;
+        int ok = 1;
+        while (ld_acquire(B.team_bar + team) < target) {
+            ++spins;
+            if ((spins & 255u) == 0) {
+                const u64 now = global_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > B.timeout_ns) {
+                    ok = 0;
+                    break;
+                }
+            }
+            if (spins > 64) __nanosleep(32);
+        }
+        __threadfence();
+        sm.ok = ok;
+    } else if (threadIdx.x == 0) {
+        sm.ok = 1;
+    }
+    __syncthreads();
+    return sm.ok != 0;
+}
+
+// Batched solves: the grid is split into teams of B.team blocks; each team
+// takes instances (largest first, as ordered by the host) from a shared
+// counter and solves each completely, with its own control block, queues and
+// state, synchronising only within the team.
+template <int L, int SW>
+__global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) batch_kernel(BatchDesc B)
+{
+    __shared__ Smem sm;
+    __shared__ unsigned s_item;
+    const unsigned team = blockIdx.x / B.team, rank = blockIdx.x % B.team;
+    u64 team_target = 0;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const unsigned item = atomicAdd(B.next, 1u);
+            B.team_item[team] = item;
+            s_item = item;
+        }
+        if (!team_sync(B, team, team_target, sm)) return;
+        if (threadIdx.x == 0 && rank != 0) s_item = __ldcg(B.team_item + team);
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item >= (unsigned)B.count) return;
+        const Params &P = B.params[item];
+        if (P.g.layout_tag == L) {
+            const u64 t0 = global_ns();
+            // the instance's control block starts at zero; then the team starts it
+            if (rank == 0) {
+                for (unsigned i = threadIdx.x; i < sizeof(Ctl) / sizeof(int); i += kBlock)
+                    ((int *)P.st.ctl)[i] = 0;
+                __threadfence();
+            }
+            if (!team_sync(B, team, team_target, sm)) return;
+            Ctx c{P, sm, 0ull, 0, B.team, rank, 0ull, 0ull, 0ull};
+            solve_instance<L, SW>(c);
+            if (rank == 0 && threadIdx.x == 0) {
+                BatchOut o;
+                o.value = __ldcg(P.st.e + P.g.t);
+                o.err = __ldcg(&P.st.ctl->err);
+                o.iterations = __ldcg(&P.st.ctl->iterations);
+                o.ns = global_ns() - t0;
+                B.out[item] = o;
+            }
+        }
+        // every block of the team has left the solve before the next grab
+        if (!team_sync(B, team, team_target, sm)) return;
+    }
 }
 
 // Edge flows in input order.  BCSR: the merged pair's net flow u -> v is
@@ -1392,6 +1524,23 @@ __global__ void edge_flow_kernel(int layout, long long m, const unsigned *arc2sl
 
 template <int L, int SW>
 static void *kernel_ptr() { return (void *)solve_kernel<L, SW>; }
+
+static void *pick_batch_kernel(int layout)
+{
+    return layout == kBCSR ? (void *)batch_kernel<kBCSR, 8> : (void *)batch_kernel<kRCSR, 8>;
+}
+
+cudaError_t batch_max_blocks_per_sm(int layout, int *blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pick_batch_kernel(layout), kBlock, 0);
+}
+
+cudaError_t batch_launch(int layout, int grid, const BatchDesc &b, cudaStream_t stream)
+{
+    BatchDesc local = b;
+    void *args[] = {&local};
+    return cudaLaunchCooperativeKernel(pick_batch_kernel(layout), dim3(grid), dim3(kBlock), args, 0, stream);
+}
 
 static void *pick_kernel(int layout, int small_tile)
 {

@@ -4,7 +4,8 @@
 //   BCSR (§3.2, Fig. 2(d)): off[n+1] (int64) rows of merged, id-sorted
 //     neighbour lists; per slot a: col[a] (int32 neighbour), cf[a] (int32
 //     residual capacity of the arc row(a) -> col[a]), cf0[a] (its initial
-//     value), rev[a] (uint32 slot of the paired entry in col[a]'s row).
+//     value), rev[a] (uint32 slot of the paired entry in col[a]'s row),
+//     cfb[a] (= cf[rev[a]], the reverse residual mirrored in place).
 //   RCSR (§3.2, Fig. 2(c)): off[n+1] out rows, per out slot j: col[j] (head),
 //     cf[j] (forward residual), bf[j] (backward residual = flow on arc j),
 //     cf0[j] (capacity); in_off[n+1] in rows, per in slot k: in_col[k]
@@ -62,16 +63,21 @@ struct __align__(128) Ctl {
     unsigned long long hub_pack[3]; // hub class: (count << 40) | total chunks
     int done;
     unsigned trace_len;
+    int gr_due_gen;      // time-balanced trigger: generation whose iteration made a
+                         // global relabel due (-1 = none)
 };
 
 struct GraphDev {
     int n, s, t;
+    int layout_tag;             // kRCSR or kBCSR (batch kernels check it)
     long long slots;
     const long long *off;
     const int *col;
     int *cf;
     const int *cf0;
     const unsigned *rev;        // BCSR, may be null when use_rev = 0
+    int *cfb;                   // BCSR with rev: cfb[a] mirrors cf[rev[a]] (residual of the
+                                // reverse arc, kept in place so BFS reads it coalesced); or null
     int *bf;                    // RCSR
     const long long *in_off;    // RCSR
     const int *in_col;          // RCSR
@@ -112,6 +118,7 @@ struct Params {
     int mode;
     long long iters_arg;
     int cycle;
+    float gr_ratio;              // > 0: global relabel once iterations took gr_ratio x its time
     int gap;
     int use_rev;
     int multi_push;
@@ -123,6 +130,27 @@ struct Params {
     unsigned long long *trace;   // optional: 4 words per grid barrier (where, gen, ns, queue total)
     int trace_cap;               // records
 };
+
+// Batched solves (solver.cu): one cooperative launch, teams of `team` blocks.
+struct BatchOut {
+    long long value;
+    long long iterations;
+    unsigned long long ns;   // device time of the instance's solve
+    int err;
+    int pad;
+};
+struct BatchDesc {
+    const Params *params;    // device array [count], largest instance first
+    int count;
+    int team;                // blocks per team (grid is a multiple of it)
+    unsigned *next;          // instance counter (zeroed before launch)
+    unsigned long long *team_bar;  // per-team barrier counters (zeroed before launch)
+    unsigned *team_item;     // per-team current instance
+    BatchOut *out;           // [count]
+    unsigned long long timeout_ns;
+};
+cudaError_t batch_max_blocks_per_sm(int layout, int *blocks);
+cudaError_t batch_launch(int layout, int grid, const BatchDesc &b, cudaStream_t stream);
 
 // Launch helpers implemented in solver.cu.
 cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks);

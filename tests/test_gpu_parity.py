@@ -248,3 +248,58 @@ def test_degenerate_graphs():
         assert got["value"] == 0 and got["flow"].tolist() == [0, 0, 0]
         got = gpu_solve(2, [0, 0, 1], [1, 1, 0], [5, 7, 3], 0, 1, layout)
         assert got["value"] == 12 and got["flow"].tolist() == [5, 7, 0]
+
+
+def _batch_instances():
+    out = []
+    for seed in range(12):
+        out.append(W.random_small(20 + 13 * seed, 150 + 40 * seed, 4200 + seed, cap_lo=0, cap_hi=30))
+    for side in (8, 16, 33):
+        out.append(W.grid(side, side, 50 + side, 1, 255, 2550))
+    for nl in (64, 300):
+        out.append(W.bipartite_poisson(nl, nl, 6, 70 + nl))
+    out.append(W.rmat(11, 16, 9))
+    out.append(W.rmat(12, 8, 10))
+    return out
+
+
+@pytest.mark.parametrize("big_slots", [1 << 20, 3000])
+def test_batch_matches_oracle(big_slots):
+    """One batched launch (single-block solves, and teams of blocks for the
+    instances above `batch_big_slots`) gives every instance its own maximum
+    flow, the same as solving it alone; edge flows are certified."""
+    m = wb()
+    insts = _batch_instances()
+    o = m.wbpr_default_options()
+    o.batch_big_slots = big_slots
+    o.batch_team = 8
+    graphs, flows, refs = [], [], []
+    for i, inst in enumerate(insts):
+        src, dst, cap = inst.numpy()
+        layout = m.WBPR_BCSR if i % 2 == 0 else m.WBPR_RCSR
+        graphs.append(m.wbpr_build(inst.n, inst.m, src, dst, cap, inst.s, inst.t, layout, o))
+        flows.append(torch.empty(max(1, inst.m), dtype=torch.int32, device="cuda:0") if i % 3 == 0 else None)
+        refs.append(oracle.maxflow_pr(inst.n, src, dst, cap, inst.s, inst.t, want_flow=False, want_cut=False)["value"])
+    values = m.wbpr_maxflow_batch(graphs, None, flows)
+    assert values == refs
+    for i, inst in enumerate(insts):
+        if flows[i] is not None:
+            src, dst, cap = inst.numpy()
+            code, cut, _ = oracle.verify_flow(inst.n, src, dst, cap, inst.s, inst.t,
+                                              flows[i][: inst.m].cpu().numpy(), values[i])
+            assert code == 0 and cut == refs[i], (i, code)
+    # a second batch on the same handles (state reused) and single solves agree
+    assert m.wbpr_maxflow_batch(graphs) == refs
+    assert [m.wbpr_maxflow(G) for G in graphs[:5]] == refs[:5]
+    for G in graphs:
+        G.close()
+
+
+@pytest.mark.parametrize("ratio", [0.0, 0.25, 1.0, 8.0])
+def test_time_balanced_relabel_same_results(ratio):
+    m = wb()
+    o = m.wbpr_default_options()
+    o.gr_ratio = ratio
+    for g in (W.rmat(12, 16, 21), W.grid(24, 24, 5)):
+        src, dst, cap = g.numpy()
+        check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
