@@ -347,6 +347,97 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """The batched / served workload: a seeded mix of grids and bipartite
+    graphs of uneven size, solved (a) one instance per launch, (b) all in one
+    batched launch, (c) through the continuous-batching server with Poisson
+    arrivals."""
+    import numpy as np
+    import torch
+    import paper_2404_00270_gb300 as wb
+    from paper_2404_00270_gb300 import serve
+    import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wb.load()
+    wb.use_torch_allocator(True)
+    stream = torch.cuda.current_stream()
+    specs = W.batch_spec(args.batch_count)
+    t0 = time.perf_counter()
+    insts = [W.make_from_spec(sp, device=dev) for sp in specs]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    total_arcs = sum(g.m for g in insts)
+    t0 = time.perf_counter()
+    graphs = [wb.wbpr_build(g.n, g.m, g.src, g.dst, g.cap, g.s, g.t, wb.WBPR_BCSR, None, stream) for g in insts]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    # (a) one instance per launch, on an evenly spaced sample
+    step = max(1, len(graphs) // args.plain_sample)
+    sample = list(range(0, len(graphs), step))
+    plain_ms, plain_vals = [], {}
+    for i in sample:
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        plain_vals[i] = wb.wbpr_maxflow(graphs[i], stream)
+        plain_ms.append(1e3 * (time.perf_counter() - ta))
+    plain_rate = len(sample) / (sum(plain_ms) / 1e3)
+    # (b) the whole mix in one batched launch per step
+    for _ in range(args.warmup):
+        vals = wb.wbpr_maxflow_batch(graphs, stream)
+    assert all(vals[i] == plain_vals[i] for i in sample)
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        vals = wb.wbpr_maxflow_batch(graphs, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    batch_rate = len(graphs) / (ms / 1e3)
+    for G in graphs:
+        G.close()
+    del graphs
+    torch.cuda.empty_cache()
+    # (c) continuous batching with Poisson arrivals at a fraction of the batch rate
+    serving = {}
+    rng = np.random.default_rng(5)
+    n_serve = min(len(insts), args.serve_count)
+    for frac in args.serve_rates:
+        lam = frac * batch_rate
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_serve))
+        reqs = [serve.Request(i, g.n, g.src, g.dst, g.cap, g.s, g.t, float(a))
+                for i, (g, a) in enumerate(zip(insts[:n_serve], arrivals))]
+        free_b, _ = torch.cuda.mem_get_info()
+        srv = serve.Server(int(0.5 * free_b), workers=2, max_batch=512)
+        out = srv.run(reqs)
+        bad = [r.rid for r in out if r.rid in plain_vals and r.value != plain_vals[r.rid]]
+        assert not bad, bad
+        summ = serve.latency_summary(out)
+        summ["rate_per_s"] = lam
+        serving[f"{frac:g}x"] = summ
+    line = {
+        "metric": "batched solves/s (4,096-instance mix, one batched launch)", "value": batch_rate,
+        "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batch-mix-{len(insts)}", "instances": len(insts), "arcs": total_arcs,
+                   "generate_s": gen_s, "build_s": build_s, "layout": "bcsr+rev",
+                   "plain_solves_per_s": plain_rate, "plain_sample": len(sample),
+                   "plain_p50_ms": float(np.percentile(plain_ms, 50)),
+                   "plain_p99_ms": float(np.percentile(plain_ms, 99)),
+                   "speedup_vs_plain": batch_rate / plain_rate,
+                   "batch_latency_p50_ms": ms, "serving": serving},
+        "roofline": None, "clocks": clocks,
+        "gpu_launches": args.steps * 2,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +448,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the benchmark workload)")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch"])
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--plain-sample", type=int, default=256)
+    ap.add_argument("--serve-count", type=int, default=1024)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 0.8, 1.0, 1.5])
     args = ap.parse_args()
+    if args.workload == "batch" and args.impl != "reference":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -75,7 +75,9 @@ typedef struct wbpr_options {
                                  rows (hubs) are split into chunks of 2048 entries
                                  that whole thread blocks take (default 1024) */
     int32_t grid_blocks;      /* persistent grid size; 0 = automatic.  Clamped to
-                                 the number of co-resident blocks. */
+                                 the number of co-resident blocks.  For
+                                 wbpr_maxflow_batch (options of the first handle)
+                                 it caps the batch grid instead. */
     int32_t barrier_timeout_ms; /* device wait limit (default 20000) */
     int64_t max_iterations;   /* cap on push-relabel iterations per solve
                                  (default 2^40); reaching it gives WBPR_ETIMEOUT */

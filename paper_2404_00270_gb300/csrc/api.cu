@@ -627,6 +627,8 @@ wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream
                 return set_error(WBPR_ECUDA, "wbpr_maxflow_batch: occupancy query failed");
             }
             long long teams = (long long)per_sm * num_sms / team;
+            // grid_blocks > 0 caps the batch grid, so several batches can share the GPU
+            if (bo.grid_blocks > 0 && bo.grid_blocks / team < teams) teams = bo.grid_blocks / team;
             if (teams > (long long)grp.size()) teams = (long long)grp.size();
             if (teams < 1) teams = 1;
             const int grid = (int)(teams * team);
