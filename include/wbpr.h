@@ -92,7 +92,7 @@ typedef struct wbpr_options {
     int32_t batch_team;       /* wbpr_maxflow_batch: blocks that solve one large
                                  instance together (power of two, default 16) */
     int64_t batch_big_slots;  /* wbpr_maxflow_batch: instances with more residual
-                                 slots than this are large (default 2^20); smaller
+                                 slots than this are large (default 2^15); smaller
                                  ones are solved by a single block each */
 } wbpr_options;
 
@@ -195,7 +195,8 @@ wbpr_status wbpr_mincut(wbpr_graph *g, wbpr_stream_t stream, int64_t *cut_value,
 wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream_t stream,
                                int64_t *values, int32_t *const *edge_flows);
 
-/* Release every device buffer of the handle.  NULL is accepted. */
+/* Release every device buffer of the handle.  NULL is accepted.  No work of
+ * the handle may be in flight (synchronise after wbpr_maxflow_async). */
 void wbpr_destroy(wbpr_graph *g);
 
 /* Options: defaults, read, replace (takes effect at the next solve). */
@@ -301,6 +302,56 @@ wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32_t s, int32
                                       const int64_t *off, const int32_t *col, const int32_t *cap,
                                       const uint32_t *rev, wbpr_stream_t stream, int64_t *d_value,
                                       int32_t *d_residual);
+
+/*
+ * Persistent server (continuous batching).  wbpr_server_start launches one
+ * long-running kernel on its own non-blocking stream.  Its blocks form
+ * `big_teams` teams of `team_blocks` blocks for large instances and
+ * `small_blocks` single-block teams for small ones.  wbpr_server_submit
+ * publishes a built handle to the queue of its size class (more than
+ * `big_slots` residual slots = large); the first free team of that class
+ * solves it at once, while other requests are being solved.  The call does
+ * not block.  wbpr_server_poll returns WBPR_OK with the flow value once the
+ * request is done, or 1 while it is pending (WBPR_ESTATE if the kernel has
+ * exited without solving it).  A handle must not be used in
+ * any other call between its submit and the poll that reports it done.
+ * wbpr_server_stop lets the running solves finish, stops the kernel (which
+ * also stops on its own after `idle_ms` without requests), and frees the
+ * server.  `idle_ms` (default 60 s) is only a safety net for a host that
+ * stopped submitting without calling wbpr_server_stop: a team that waited
+ * that long for its next request leaves the kernel, and a request published
+ * to its queue position afterwards is never solved (its poll then reports
+ * WBPR_ESTATE).  The rings hold `capacity` requests per class for the lifetime of
+ * the server.  Only handles with the server's layout are accepted.
+ * Host-mapped pinned memory carries requests and results (no device
+ * round trip per request).  Leave room on the SMs: a build launched while
+ * the server runs needs resident space for its own blocks, and it waits for
+ * the server to exit otherwise.  Its radix-sort blocks need about 37 K
+ * registers, more than an SM holding two server blocks (16 K each) has left,
+ * so the defaults use one server block per SM (4 teams of 16 blocks and 88
+ * single-block teams on 152 SMs).  wbpr_maxflow_batch builds nothing while
+ * its server runs and uses every resident slot.
+ */
+typedef struct wbpr_server wbpr_server;
+typedef struct wbpr_server_options {
+    int32_t layout;        /* WBPR_RCSR or WBPR_BCSR */
+    int32_t capacity;      /* requests per class over the server's lifetime */
+    int32_t team_blocks;   /* blocks per large-instance team (power of two) */
+    int32_t big_teams;     /* large-instance teams */
+    int32_t small_blocks;  /* single-block teams */
+    int32_t idle_ms;       /* the kernel stops after this long without requests */
+    int64_t big_slots;     /* class boundary in residual slots */
+} wbpr_server_options;
+void wbpr_server_default_options(wbpr_server_options *opts);
+wbpr_server *wbpr_server_start(const wbpr_server_options *opts);
+int64_t wbpr_server_submit(wbpr_server *srv, wbpr_graph *g);  /* ticket >= 0, or a negative wbpr_status */
+wbpr_status wbpr_server_poll(wbpr_server *srv, int64_t ticket, int64_t *value);
+wbpr_status wbpr_server_stop(wbpr_server *srv);
+/* Diagnostics once the server kernel has ended (1 while it still runs): for
+ * each of the first `count` teams (large teams first, then single blocks) why
+ * it left: 0 still running, 1 end of its ring, 2 stop flag, 3 idle limit,
+ * 4-6 a team barrier gave up. */
+wbpr_status wbpr_server_team_exits(wbpr_server *srv, int32_t *reasons, int32_t count);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,8 @@ EXPORTED_SYMBOLS = [
     "wbpr_get_options", "wbpr_set_options", "wbpr_get_stats", "wbpr_get_info",
     "wbpr_last_error", "wbpr_last_error_message", "wbpr_error_string", "wbpr_set_allocator",
     "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc",
+    "wbpr_server_default_options", "wbpr_server_start", "wbpr_server_submit", "wbpr_server_poll",
+    "wbpr_server_stop", "wbpr_server_team_exits",
 ]
 
 
@@ -138,10 +140,20 @@ def load(build_if_missing: bool = False):
         lib.wbpr_run_stage.argtypes = [_P, _P, i32, i64]
         lib.wbpr_export.argtypes = [_P, i32, _P, i64]
         lib.wbpr_maxflow_bcsr_noalloc.argtypes = [i32, i64, i32, i32, _P, _P, _P, _P, _P, _P, _P]
+        lib.wbpr_server_default_options.argtypes = [_P]
+        lib.wbpr_server_default_options.restype = None
+        lib.wbpr_server_start.argtypes = [_P]
+        lib.wbpr_server_start.restype = _P
+        lib.wbpr_server_submit.argtypes = [_P, _P]
+        lib.wbpr_server_submit.restype = i64
+        lib.wbpr_server_poll.argtypes = [_P, i64, _P]
+        lib.wbpr_server_stop.argtypes = [_P]
+        lib.wbpr_server_team_exits.argtypes = [_P, _P, i32]
         for name in ("wbpr_maxflow", "wbpr_maxflow_async", "wbpr_solve_status", "wbpr_mincut",
                      "wbpr_maxflow_batch", "wbpr_get_options", "wbpr_set_options",
                      "wbpr_get_stats", "wbpr_get_info", "wbpr_last_error", "wbpr_set_allocator",
-                     "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc"):
+                     "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc", "wbpr_server_poll",
+                     "wbpr_server_stop", "wbpr_server_team_exits"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
         return lib
@@ -232,6 +244,10 @@ def use_torch_allocator(enable: bool = True):
     cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
     _check(lib.wbpr_set_allocator(ctypes.cast(cbs[0], _P), ctypes.cast(cbs[1], _P), None))
     _ALLOC_CBS = cbs
+
+
+def torch_allocator_enabled() -> bool:
+    return _ALLOC_CBS is not None
 
 
 def wbpr_default_options() -> Options:
@@ -362,3 +378,54 @@ def wbpr_maxflow_bcsr_noalloc(n, slots, s, t, off, col, cap, rev, stream=None, d
     br, bv, bres = _Buf(rev, np.int32), _Buf(d_value, np.int64), _Buf(d_residual, np.int32)
     _check(load().wbpr_maxflow_bcsr_noalloc(int(n), int(slots), int(s), int(t), bo.ptr, bc.ptr, bk.ptr,
                                             br.ptr, _stream(stream), bv.ptr, bres.ptr))
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_int32), ("capacity", ctypes.c_int32), ("team_blocks", ctypes.c_int32),
+                ("big_teams", ctypes.c_int32), ("small_blocks", ctypes.c_int32), ("idle_ms", ctypes.c_int32),
+                ("big_slots", ctypes.c_int64)]
+
+
+def wbpr_server_default_options() -> ServerOptions:
+    o = ServerOptions()
+    load().wbpr_server_default_options(ctypes.byref(o))
+    return o
+
+
+def wbpr_server_start(opts: ServerOptions | None = None) -> int:
+    lib = load()
+    h = lib.wbpr_server_start(ctypes.byref(opts) if opts is not None else None)
+    if not h:
+        raise WbprError(lib.wbpr_last_error(), (lib.wbpr_last_error_message() or b"").decode())
+    return h
+
+
+def wbpr_server_submit(server: int, g: Graph) -> int:
+    t = load().wbpr_server_submit(server, g.handle)
+    if t < 0:
+        _check(int(t))
+    return int(t)
+
+
+def wbpr_server_poll(server: int, ticket: int):
+    """The flow value once the request is done, else None."""
+    v = ctypes.c_int64(0)
+    rc = load().wbpr_server_poll(server, int(ticket), ctypes.byref(v))
+    if rc == 1:
+        return None
+    _check(rc)
+    return v.value
+
+
+def wbpr_server_stop(server: int) -> None:
+    _check(load().wbpr_server_stop(server))
+
+
+def wbpr_server_team_exits(server: int, count: int):
+    """Exit reason per team once the server kernel has ended, else None."""
+    out = (ctypes.c_int32 * max(1, count))()
+    rc = load().wbpr_server_team_exits(server, out, int(count))
+    if rc == 1:
+        return None
+    _check(rc)
+    return list(out)[:count]

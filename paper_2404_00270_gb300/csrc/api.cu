@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -42,8 +43,9 @@ wbpr_status set_error(wbpr_status st, const std::string &msg)
     return st;
 }
 
-void *dev_alloc(size_t bytes, cudaStream_t stream)
+void *dev_alloc(size_t bytes, cudaStream_t stream, DevFree *owner)
 {
+    if (owner) *owner = DevFree{g_free, g_ctx};
     if (g_alloc) return g_alloc(bytes, (wbpr_stream_t)stream, g_ctx);
     void *p = nullptr;
     if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
@@ -53,11 +55,13 @@ void *dev_alloc(size_t bytes, cudaStream_t stream)
     return p;
 }
 
-void dev_free(void *p, size_t bytes, cudaStream_t stream)
+void dev_free(void *p, size_t bytes, cudaStream_t stream, const DevFree *owner)
 {
     if (!p) return;
-    if (g_free) {
-        g_free(p, bytes, (wbpr_stream_t)stream, g_ctx);
+    const wbpr_free_fn fn = owner ? owner->fn : g_free;
+    void *ctx = owner ? owner->ctx : g_ctx;
+    if (fn) {
+        fn(p, bytes, (wbpr_stream_t)stream, ctx);
         return;
     }
     cudaFreeAsync(p, stream);
@@ -93,7 +97,7 @@ void wbpr_default_options(wbpr_options *o)
     o->trace = 0;
     o->gr_ratio = 1.0f;
     o->batch_team = 16;
-    o->batch_big_slots = (int64_t)1 << 20;
+    o->batch_big_slots = (int64_t)1 << 15;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -146,10 +150,13 @@ void wbpr_destroy(wbpr_graph *g)
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
-    cudaDeviceSynchronize();
-    for (auto &b : g->blocks) dev_free(b.p, b.bytes, 0);
+    // Not a device-wide sync: a persistent server kernel may be running on a
+    // non-blocking stream.  The caller guarantees no work of this handle is in
+    // flight (every synchronous call has finished it).
     cudaStreamSynchronize(0);
-    if (g->pinned) cudaFreeHost(g->pinned);
+    for (auto &b : g->blocks) dev_free(b.p, b.bytes, 0, &b.owner);
+    cudaStreamSynchronize(0);
+    delete[] g->pinned;
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     cudaGetLastError();
@@ -245,10 +252,12 @@ wbpr_graph *wbpr_build_ex(int64_t n, int64_t m, const int32_t *src, const int32_
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
     if (!coop) return fail(WBPR_ECUDA, "wbpr_build: device lacks cooperative launch");
-    if (cudaMallocHost(&g->pinned, 64 * sizeof(long long)) != cudaSuccess) {
-        cudaGetLastError();
-        g->pinned = nullptr;
-        return fail(WBPR_ENOMEM, "wbpr_build: pinned host allocation failed");
+    // Host staging of small results: ordinary heap memory.  A pinned
+    // allocation here would synchronise with every stream (including a
+    // running persistent server kernel).
+    g->pinned = new (std::nothrow) long long[64];
+    if (!g->pinned) {
+        return fail(WBPR_ENOMEM, "wbpr_build: host allocation failed");
     }
     cudaEventCreate(&g->ev0);
     cudaEventCreate(&g->ev1);
@@ -365,7 +374,7 @@ static int choose_grid(wbpr_graph *g)
     return grid;
 }
 
-static Params make_params(wbpr_graph *g, int mode)
+Params make_params(wbpr_graph *g, int mode)
 {
     Params p;
     memset(&p, 0, sizeof(p));
@@ -580,127 +589,6 @@ wbpr_status wbpr_mincut(wbpr_graph *g, wbpr_stream_t stream, int64_t *cut_value,
     g->solved_flow = true;
     g->solved_value = true;
     return WBPR_OK;
-}
-
-wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream_t stream, int64_t *values,
-                               int32_t *const *edge_flows)
-{
-    if (count < 0 || (count > 0 && (!gs || !values)))
-        return set_error(WBPR_EINVAL, "wbpr_maxflow_batch: bad arguments");
-    int device = 0;
-    if (count > 0 && cudaGetDevice(&device) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(WBPR_ECUDA, "wbpr_maxflow_batch: no CUDA device");
-    }
-    for (int i = 0; i < count; ++i) {
-        if (!gs[i]) return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: NULL handle");
-        if (gs[i]->device != device) return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: handle of another device");
-    }
-    {
-        std::vector<const wbpr_graph *> sorted(gs, gs + count);
-        std::sort(sorted.begin(), sorted.end());
-        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
-            return set_error(WBPR_ESTATE, "wbpr_maxflow_batch: repeated handle");
-    }
-    if (count == 0) return WBPR_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const wbpr_options &bo = gs[0]->opts;
-    const int num_sms = gs[0]->num_sms;
-    // groups: (layout, large?) -- large instances first, largest first within a group
-    std::vector<int> groups[2][2];
-    for (int i = 0; i < count; ++i) {
-        const int lay = gs[i]->layout == WBPR_BCSR ? 1 : 0;
-        const int big = gs[i]->slots > bo.batch_big_slots ? 1 : 0;
-        groups[lay][big].push_back(i);
-    }
-    std::vector<BatchOut> outs((size_t)count);
-    for (int big = 1; big >= 0; --big) {
-        for (int lay = 0; lay < 2; ++lay) {
-            std::vector<int> &grp = groups[lay][big];
-            if (grp.empty()) continue;
-            std::stable_sort(grp.begin(), grp.end(), [&](int a, int b) { return gs[a]->slots > gs[b]->slots; });
-            const int team = big ? bo.batch_team : 1;
-            const int layout = lay ? kBCSR : kRCSR;
-            int per_sm = 0;
-            if (batch_max_blocks_per_sm(layout, &per_sm) != cudaSuccess || per_sm < 1) {
-                cudaGetLastError();
-                return set_error(WBPR_ECUDA, "wbpr_maxflow_batch: occupancy query failed");
-            }
-            long long teams = (long long)per_sm * num_sms / team;
-            // grid_blocks > 0 caps the batch grid, so several batches can share the GPU
-            if (bo.grid_blocks > 0 && bo.grid_blocks / team < teams) teams = bo.grid_blocks / team;
-            if (teams > (long long)grp.size()) teams = (long long)grp.size();
-            if (teams < 1) teams = 1;
-            const int grid = (int)(teams * team);
-            const size_t n_items = grp.size();
-            std::vector<Params> hp(n_items);
-            for (size_t j = 0; j < n_items; ++j) {
-                wbpr_graph *g = gs[grp[j]];
-                const bool want_flow = edge_flows && edge_flows[grp[j]];
-                hp[j] = make_params(g, kModePreflow | kModePhase1 | (want_flow ? kModePhase2 : 0));
-                g->grid_blocks = team;
-            }
-            const size_t bytes_p = sizeof(Params) * n_items, bytes_o = sizeof(BatchOut) * n_items;
-            const size_t bytes_c = 256 + 16 * (size_t)teams;
-            Params *dp = (Params *)dev_alloc(bytes_p, st);
-            BatchOut *dout = (BatchOut *)dev_alloc(bytes_o, st);
-            unsigned char *dc = (unsigned char *)dev_alloc(bytes_c, st);
-            auto release = [&]() {
-                dev_free(dp, bytes_p, st);
-                dev_free(dout, bytes_o, st);
-                dev_free(dc, bytes_c, st);
-            };
-            if (!dp || !dout || !dc) {
-                release();
-                return set_error(WBPR_ENOMEM, "wbpr_maxflow_batch: device allocation failed");
-            }
-            BatchDesc b;
-            memset(&b, 0, sizeof(b));
-            b.params = dp;
-            b.count = (int)n_items;
-            b.team = team;
-            b.next = (unsigned *)dc;
-            b.team_bar = (unsigned long long *)(dc + 256);
-            b.team_item = (unsigned *)(dc + 256 + 8 * (size_t)teams);
-            b.out = dout;
-            b.timeout_ns = (unsigned long long)bo.barrier_timeout_ms * 1000000ull;
-            cudaError_t e = cudaMemcpyAsync(dp, hp.data(), bytes_p, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, bytes_c, st);
-            if (e == cudaSuccess) e = batch_launch(layout, grid, b, st);
-            std::vector<BatchOut> ho(n_items);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(ho.data(), dout, bytes_o, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            release();
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return set_error(WBPR_ECUDA, std::string("wbpr_maxflow_batch: ") + cudaGetErrorString(e));
-            }
-            for (size_t j = 0; j < n_items; ++j) outs[(size_t)grp[j]] = ho[j];
-        }
-    }
-    wbpr_status rc = WBPR_OK;
-    for (int i = 0; i < count; ++i) {
-        wbpr_graph *g = gs[i];
-        const BatchOut &o = outs[(size_t)i];
-        memset(&g->stats, 0, sizeof(g->stats));
-        g->stats.iterations = o.iterations;
-        g->stats.solve_ms = (double)o.ns * 1e-6;
-        if (o.err != 0) {
-            g->solved_flow = g->solved_value = false;
-            if (rc == WBPR_OK)
-                rc = set_error((wbpr_status)o.err, "wbpr_maxflow_batch: instance " + std::to_string(i) + " gave up");
-            continue;
-        }
-        values[i] = o.value;
-        const bool want_flow = edge_flows && edge_flows[i];
-        g->solved_value = true;
-        g->solved_flow = want_flow;
-        if (want_flow)
-            API_CUDA(launch_edge_flow(g->layout, g->m, g->arc2slot, g->cf0, g->cf, g->bf, g->prefix, g->cap_in,
-                                      edge_flows[i], st));
-    }
-    API_CUDA(cudaStreamSynchronize(st));
-    return rc;
 }
 
 wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg)

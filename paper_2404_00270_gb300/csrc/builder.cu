@@ -228,28 +228,34 @@ inline int bitlen(long long x)
 
 // Scratch allocations released at the end of the build.
 struct Scratch {
+    struct Held {
+        void *p;
+        size_t bytes;
+        DevFree owner;
+    };
     cudaStream_t st;
-    std::vector<std::pair<void *, size_t>> held;
+    std::vector<Held> held;
     explicit Scratch(cudaStream_t s) : st(s) {}
     void *get(size_t bytes)
     {
         if (bytes == 0) bytes = 16;
-        void *p = dev_alloc(bytes, st);
-        if (p) held.push_back({p, bytes});
+        DevFree owner;
+        void *p = dev_alloc(bytes, st, &owner);
+        if (p) held.push_back({p, bytes, owner});
         return p;
     }
     void release(void *p)
     {
         for (size_t i = 0; i < held.size(); ++i)
-            if (held[i].first == p) {
-                dev_free(p, held[i].second, st);
+            if (held[i].p == p) {
+                dev_free(p, held[i].bytes, st, &held[i].owner);
                 held.erase(held.begin() + (long)i);
                 return;
             }
     }
     ~Scratch()
     {
-        for (auto &b : held) dev_free(b.first, b.second, st);
+        for (auto &b : held) dev_free(b.p, b.bytes, st, &b.owner);
     }
 };
 

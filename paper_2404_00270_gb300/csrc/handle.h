@@ -12,9 +12,16 @@
 
 namespace wbpr {
 
-// Device allocation through the allocator hook (api.cu).  Returns null on failure.
-void *dev_alloc(size_t bytes, cudaStream_t stream);
-void dev_free(void *p, size_t bytes, cudaStream_t stream);
+// Device allocation through the allocator hook (api.cu).  Returns null on
+// failure.  `owner` (optional) records the free function in force at
+// allocation time, so a block is always returned to the allocator that made
+// it even if the hook changes in between.
+struct DevFree {
+    wbpr_free_fn fn;
+    void *ctx;
+};
+void *dev_alloc(size_t bytes, cudaStream_t stream, DevFree *owner = nullptr);
+void dev_free(void *p, size_t bytes, cudaStream_t stream, const DevFree *owner = nullptr);
 
 // Records a failure for wbpr_last_error()/wbpr_last_error_message().
 wbpr_status set_error(wbpr_status st, const std::string &msg);
@@ -69,12 +76,13 @@ struct wbpr_graph {
     int *edge_tmp = nullptr;           // device staging of edge flows for host outputs
     unsigned char *side_tmp = nullptr; // device staging of the cut side for host outputs
     // host
-    long long *pinned = nullptr;       // small pinned staging buffer
+    long long *pinned = nullptr;       // host staging of small results (64 words)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
     struct Block {
         void *p;
         size_t bytes;
+        wbpr::DevFree owner;
     };
     std::vector<Block> blocks;  // every device allocation owned by the handle
     int64_t device_bytes = 0;
@@ -82,9 +90,10 @@ struct wbpr_graph {
     void *alloc(size_t bytes, cudaStream_t st)
     {
         if (bytes == 0) bytes = 16;
-        void *p = wbpr::dev_alloc(bytes, st);
+        wbpr::DevFree owner;
+        void *p = wbpr::dev_alloc(bytes, st, &owner);
         if (p) {
-            blocks.push_back({p, bytes});
+            blocks.push_back({p, bytes, owner});
             device_bytes += (int64_t)bytes;
         }
         return p;
@@ -95,4 +104,6 @@ namespace wbpr {
 // Graph builders (builder.cu).  The inputs are device pointers.
 wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int *cap,
                         cudaStream_t stream);
+// Solver parameters of a handle for the given launch modes (api.cu).
+Params make_params(wbpr_graph *g, int mode);
 }  // namespace wbpr

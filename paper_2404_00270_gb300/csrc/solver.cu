@@ -1411,23 +1411,24 @@ __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) solve_kernel(Params P
     solve_instance<L, SW>(c);
 }
 
-// Team barrier of the batch kernel (teams of more than one block).
-__device__ bool team_sync(const BatchDesc &B, unsigned team, u64 &target, Smem &sm)
+// Barrier over a team of `tsize` blocks (counter `bar`); a single-block team
+// is just __syncthreads.  Gives up after `limit_ns`.
+__device__ bool team_sync(u64 *bar, unsigned tsize, u64 limit_ns, u64 &target, Smem &sm)
 {
     __syncthreads();
-    if (B.team > 1 && threadIdx.x == 0) {
-        target += B.team;
+    if (tsize > 1 && threadIdx.x == 0) {
+        target += tsize;
         __threadfence();
-        atomicAdd(B.team_bar + team, 1ULL);
+        atomicAdd(bar, 1ULL);
         u64 t0 = 0;
         unsigned spins = 0;
         int ok = 1;
-        while (ld_acquire(B.team_bar + team) < target) {
+        while (ld_acquire(bar) < target) {
             ++spins;
             if ((spins & 255u) == 0) {
                 const u64 now = global_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > B.timeout_ns) {
+                else if (now - t0 > limit_ns) {
                     ok = 0;
                     break;
                 }
@@ -1443,51 +1444,142 @@ __device__ bool team_sync(const BatchDesc &B, unsigned team, u64 &target, Smem &
     return sm.ok != 0;
 }
 
-// Batched solves: the grid is split into teams of B.team blocks; each team
-// takes instances (largest first, as ordered by the host) from a shared
-// counter and solves each completely, with its own control block, queues and
-// state, synchronising only within the team.
+__device__ __forceinline__ unsigned ld_acquire_sys_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys_s32(int *p, int v)
+{
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Persistent server: teams wait for requests that the host publishes in
+// host-mapped rings (one ring per size class), solve each completely and
+// publish the result, until the host raises `stop` or no request has come
+// for `idle_ns`.  Blocks [0, n_big_teams * team_big) form teams of team_big
+// blocks (class 1, large instances); every other block is a team of one
+// (class 0, small instances).
 template <int L, int SW>
-__global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) batch_kernel(BatchDesc B)
+__global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) server_kernel(ServerDesc D)
 {
     __shared__ Smem sm;
+    __shared__ Params sp;
     __shared__ unsigned s_item;
-    const unsigned team = blockIdx.x / B.team, rank = blockIdx.x % B.team;
-    u64 team_target = 0;
+    constexpr unsigned kExit = 0xffffffffu;
+    const unsigned nbig = (unsigned)(D.n_big_teams * D.team_big);
+    int cls;
+    unsigned team, rank, tsize;
+    if (blockIdx.x < nbig) {
+        cls = 1;
+        team = blockIdx.x / D.team_big;
+        rank = blockIdx.x % D.team_big;
+        tsize = D.team_big;
+    } else {
+        cls = 0;
+        team = D.n_big_teams + (blockIdx.x - nbig);
+        rank = 0;
+        tsize = 1;
+    }
+    const u64 team_limit = D.idle_ns + D.timeout_ns;
+    u64 target = 0;
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
-            const unsigned item = atomicAdd(B.next, 1u);
-            B.team_item[team] = item;
+            // Claim the next request only once the host has published it, so a
+            // team that leaves (stop flag, idle limit) never strands one.
+            unsigned item = kExit;
+            const u64 t0 = global_ns();
+            unsigned spins = 0;
+            for (;;) {
+                const unsigned cur = *(volatile unsigned *)(D.next[cls]);
+                if (cur >= D.capacity[cls]) {
+                    D.team_exit[team] = 1;
+                    break;
+                }
+                if ((u64)cur < ld_acquire((const u64 *)(D.mirror + 2 * cls))) {
+                    if (atomicCAS(D.next[cls], cur, cur + 1) == cur) {
+                        item = cur;
+                        break;
+                    }
+                    continue;
+                }
+                // Waiting leaders watch device-memory mirrors of the host's
+                // counters; one elected poller at a time refreshes them from the
+                // host-mapped words (system-scope loads are costly, and hundreds
+                // of leaders issuing them continuously starve other work).
+                // The host publishes requests before it raises stop; the poller
+                // reads stop first and mirrors the counts before stop, so a
+                // leader that sees stop and then re-reads the count sees every
+                // request published before it.
+                if (ld_acquire((const u64 *)(D.mirror + 4)) != 0) {
+                    if ((u64)cur < ld_acquire((const u64 *)(D.mirror + 2 * cls))) continue;
+                    D.team_exit[team] = 2;
+                    break;
+                }
+                if (atomicCAS(D.poll_token, 0, 1) == 0) {
+                    const unsigned st = ld_acquire_sys_u32((const unsigned *)D.stop);
+                    const unsigned a0 = ld_acquire_sys_u32(D.avail[0]);
+                    const unsigned a1 = ld_acquire_sys_u32(D.avail[1]);
+                    atomicMax((u64 *)(D.mirror + 0), (u64)a0);
+                    atomicMax((u64 *)(D.mirror + 2), (u64)a1);
+                    __threadfence();
+                    if (st) atomicExch((u64 *)(D.mirror + 4), 1ull);
+                    __threadfence();
+                    atomicExch(D.poll_token, 0);
+                    continue;
+                }
+                if ((++spins & 63u) == 0 && global_ns() - t0 > D.idle_ns) {
+                    D.team_exit[team] = 3;
+                    break;
+                }
+                __nanosleep(500);
+            }
+            D.team_item[team] = item;
             s_item = item;
         }
-        if (!team_sync(B, team, team_target, sm)) return;
-        if (threadIdx.x == 0 && rank != 0) s_item = __ldcg(B.team_item + team);
+        if (!team_sync(D.team_bar + team, tsize, team_limit, target, sm)) {
+            if (threadIdx.x == 0) D.team_exit[team] = 4;
+            return;
+        }
+        if (threadIdx.x == 0 && rank != 0) s_item = __ldcg(D.team_item + team);
         __syncthreads();
         const unsigned item = s_item;
-        if (item >= (unsigned)B.count) return;
-        const Params &P = B.params[item];
+        if (item == kExit) return;
+        __threadfence_system();
+        const int *src = (const int *)(D.ring[cls] + item);
+        for (unsigned i = threadIdx.x; i < sizeof(Params) / sizeof(int); i += kBlock) ((int *)&sp)[i] = src[i];
+        __syncthreads();
+        const Params &P = sp;
+        const u64 t_start = global_ns();
         if (P.g.layout_tag == L) {
-            const u64 t0 = global_ns();
-            // the instance's control block starts at zero; then the team starts it
             if (rank == 0) {
-                for (unsigned i = threadIdx.x; i < sizeof(Ctl) / sizeof(int); i += kBlock)
-                    ((int *)P.st.ctl)[i] = 0;
+                for (unsigned i = threadIdx.x; i < sizeof(Ctl) / sizeof(int); i += kBlock) ((int *)P.st.ctl)[i] = 0;
                 __threadfence();
             }
-            if (!team_sync(B, team, team_target, sm)) return;
-            Ctx c{P, sm, 0ull, 0, B.team, rank, 0ull, 0ull, 0ull};
-            solve_instance<L, SW>(c);
-            if (rank == 0 && threadIdx.x == 0) {
-                BatchOut o;
-                o.value = __ldcg(P.st.e + P.g.t);
-                o.err = __ldcg(&P.st.ctl->err);
-                o.iterations = __ldcg(&P.st.ctl->iterations);
-                o.ns = global_ns() - t0;
-                B.out[item] = o;
+            if (!team_sync(D.team_bar + team, tsize, team_limit, target, sm)) {
+                if (threadIdx.x == 0) D.team_exit[team] = 5;
+                return;
             }
+            Ctx c{P, sm, 0ull, 0, tsize, rank, 0ull, 0ull, 0ull};
+            solve_instance<L, SW>(c);
         }
-        // every block of the team has left the solve before the next grab
-        if (!team_sync(B, team, team_target, sm)) return;
+        if (rank == 0 && threadIdx.x == 0) {
+            ServerOut *o = D.out[cls] + item;
+            const bool ran = P.g.layout_tag == L;
+            o->value = ran ? __ldcg(P.st.e + P.g.t) : -1;
+            o->iterations = ran ? __ldcg(&P.st.ctl->iterations) : 0;
+            o->err = ran ? __ldcg(&P.st.ctl->err) : (int)WBPR_ESTATE;
+            o->t_start = t_start;
+            o->t_end = global_ns();
+            __threadfence_system();
+            st_release_sys_s32(&o->done, 1);
+        }
+        if (!team_sync(D.team_bar + team, tsize, team_limit, target, sm)) {
+            if (threadIdx.x == 0) D.team_exit[team] = 6;
+            return;
+        }
     }
 }
 
@@ -1525,22 +1617,23 @@ __global__ void edge_flow_kernel(int layout, long long m, const unsigned *arc2sl
 template <int L, int SW>
 static void *kernel_ptr() { return (void *)solve_kernel<L, SW>; }
 
-static void *pick_batch_kernel(int layout)
+static void *pick_server_kernel(int layout)
 {
-    return layout == kBCSR ? (void *)batch_kernel<kBCSR, 8> : (void *)batch_kernel<kRCSR, 8>;
+    return layout == kBCSR ? (void *)server_kernel<kBCSR, 8> : (void *)server_kernel<kRCSR, 8>;
 }
 
-cudaError_t batch_max_blocks_per_sm(int layout, int *blocks)
+cudaError_t server_max_blocks_per_sm(int layout, int *blocks)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pick_batch_kernel(layout), kBlock, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pick_server_kernel(layout), kBlock, 0);
 }
 
-cudaError_t batch_launch(int layout, int grid, const BatchDesc &b, cudaStream_t stream)
+cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream)
 {
-    BatchDesc local = b;
+    ServerDesc local = d;
     void *args[] = {&local};
-    return cudaLaunchCooperativeKernel(pick_batch_kernel(layout), dim3(grid), dim3(kBlock), args, 0, stream);
+    return cudaLaunchCooperativeKernel(pick_server_kernel(layout), dim3(grid), dim3(kBlock), args, 0, stream);
 }
+
 
 static void *pick_kernel(int layout, int small_tile)
 {

@@ -131,26 +131,34 @@ struct Params {
     int trace_cap;               // records
 };
 
-// Batched solves (solver.cu): one cooperative launch, teams of `team` blocks.
-struct BatchOut {
+// Persistent server (solver.cu).  The rings, results, published counts and
+// stop flag live in host-mapped pinned memory (device pointers here).
+struct ServerOut {
     long long value;
     long long iterations;
-    unsigned long long ns;   // device time of the instance's solve
+    unsigned long long t_start, t_end;  // globaltimer ns
     int err;
-    int pad;
+    int done;                           // written last (release, system scope)
 };
-struct BatchDesc {
-    const Params *params;    // device array [count], largest instance first
-    int count;
-    int team;                // blocks per team (grid is a multiple of it)
-    unsigned *next;          // instance counter (zeroed before launch)
-    unsigned long long *team_bar;  // per-team barrier counters (zeroed before launch)
-    unsigned *team_item;     // per-team current instance
-    BatchOut *out;           // [count]
+struct ServerDesc {
+    const Params *ring[2];
+    ServerOut *out[2];
+    const unsigned *avail[2];
+    const int *stop;
+    unsigned *next[2];
+    unsigned long long *team_bar;
+    unsigned *team_item;
+    unsigned *mirror;        // device copies (u64 each): avail[0] at +0, avail[1] at +2, stop at +4
+    int *poll_token;         // 1 while one leader refreshes the mirror from host memory
+    int *team_exit;          // why each team left: 1 ring end, 2 stop, 3 idle, 4-6 team barrier limit
+    unsigned capacity[2];
+    int team_big;
+    int n_big_teams;
+    unsigned long long idle_ns;
     unsigned long long timeout_ns;
 };
-cudaError_t batch_max_blocks_per_sm(int layout, int *blocks);
-cudaError_t batch_launch(int layout, int grid, const BatchDesc &b, cudaStream_t stream);
+cudaError_t server_max_blocks_per_sm(int layout, int *blocks);
+cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream);
 
 // Launch helpers implemented in solver.cu.
 cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks);

@@ -1,29 +1,28 @@
 """Continuous-batching server for max-flow / matching requests.
 
-Host-side scheduling only; every solve runs in the CUDA library through
-``wbpr_maxflow_batch``.  Requests arrive over time (their graphs already
-resident on the device as COO arrays).  The admission loop builds a request's
-residual graph (``wbpr_build``) as soon as the device-memory footprint of the
-requests in flight leaves room for it, and keeps it resident until its solve
-returns.  Worker threads, each with its own CUDA stream and a slice of the
-GPU (``grid_blocks``), repeatedly take every admitted request that is waiting
-(up to ``max_batch``) and solve them together in one batched launch.  So
-requests that arrive while others are on the GPU join the next batch of any
-worker that frees up, and the batches of different workers overlap on the
-device.  Latency is measured from a request's arrival to the return of its
-batch.
+Host-side admission only; every solve runs in the library's persistent
+server kernel (``wbpr_server_start``).  Requests arrive over time with their
+graphs already on the device as COO arrays.  The admission loop builds a
+request's residual graph (``wbpr_build``) as soon as the device-memory
+footprint of the requests in flight leaves room for it, and publishes it to
+the kernel (``wbpr_server_submit``).  The kernel's first free team of the
+request's size class starts solving it at once, while other requests are
+still being solved.  The graph stays resident until its result is polled
+(``wbpr_server_poll``), which frees its memory for the next admissions.
+Latency is measured from a request's arrival to the poll that sees it done.
 """
 from __future__ import annotations
 
 import collections
 import dataclasses
-import threading
 import time
 
 import torch
 
-from . import (WBPR_BCSR, wbpr_build, wbpr_default_options, wbpr_get_info, wbpr_maxflow_batch,
-               load)
+from . import (WBPR_BCSR, load, torch_allocator_enabled, use_torch_allocator, wbpr_build,
+               wbpr_get_info, wbpr_server_default_options,
+               wbpr_server_poll, wbpr_server_start, wbpr_server_stop, wbpr_server_submit,
+               wbpr_server_team_exits)
 
 
 @dataclasses.dataclass
@@ -40,6 +39,7 @@ class Request:
     admitted: float | None = None
     done: float | None = None
     footprint: int = 0
+    build_ms: float = 0.0
 
     @property
     def m(self) -> int:
@@ -53,95 +53,107 @@ def footprint_estimate(n: int, m: int) -> int:
 
 
 class Server:
-    def __init__(self, memory_budget: int, workers: int = 2, max_batch: int = 512,
-                 layout: int = WBPR_BCSR, device=None):
+    """Admission by footprint in front of the persistent server kernel."""
+
+    def __init__(self, memory_budget: int, layout: int = WBPR_BCSR, big_slots: int = 1 << 15,
+                 team_blocks: int = 16, big_teams: int | None = None, small_blocks: int | None = None,
+                 idle_ms: int = 60000, device=None):
         load()
         self.device = torch.device(device or "cuda", torch.cuda.current_device())
         self.budget = int(memory_budget)
-        self.workers = workers
-        self.max_batch = max_batch
         self.layout = layout
-        per_worker = 0
-        props = torch.cuda.get_device_properties(self.device)
-        # each worker's batches get an equal slice of the co-resident blocks
-        per_worker = max(1, (props.multi_processor_count * 4) // workers)
-        self.opts = wbpr_default_options()
-        self.opts.grid_blocks = per_worker
-        self._lock = threading.Condition()
-        self._ready = collections.deque()
-        self._in_use = 0
-        self._stop = False
-        self.batches = []
+        self.opts = wbpr_server_default_options()
+        self.opts.layout = layout
+        self.opts.big_slots = big_slots
+        # one server block per SM: the rest of every SM stays free for the
+        # builds that admission runs while the server kernel is resident (a
+        # build's radix-sort block needs more registers than two server blocks
+        # leave on an SM)
+        total = torch.cuda.get_device_properties(self.device).multi_processor_count
+        if big_teams is None:
+            big_teams = max(1, total // 2 // team_blocks)
+        if small_blocks is None:
+            small_blocks = max(1, total - big_teams * team_blocks)
+        self.opts.team_blocks = team_blocks
+        self.opts.big_teams = big_teams
+        self.opts.small_blocks = small_blocks
+        self.opts.idle_ms = idle_ms
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.stall_s = 120.0
 
-    # -- worker ---------------------------------------------------------------
-    def _worker(self, t0: float):
-        stream = torch.cuda.Stream(device=self.device)
-        torch.cuda.set_device(self.device)
-        while True:
-            with self._lock:
-                while not self._ready and not self._stop:
-                    self._lock.wait(0.01)
-                if not self._ready and self._stop:
-                    return
-                batch = []
-                while self._ready and len(batch) < self.max_batch:
-                    batch.append(self._ready.popleft())
-            handles = [g for _, g in batch]
-            values = wbpr_maxflow_batch(handles, stream)
-            now = time.perf_counter() - t0
-            for (req, g), v in zip(batch, values):
-                req.value = v
-                req.done = now
-                g.close()
-            with self._lock:
-                for req, _ in batch:
-                    self._in_use -= req.footprint
-                self.batches.append((now, len(batch)))
-                self._lock.notify_all()
-
-    # -- admission loop ---------------------------------------------------------
-    def run(self, requests):
+    def run(self, requests, max_inflight: int = 1 << 30):
         """Serve `requests` (sorted by arrival); returns them with results."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        self.opts.capacity = max(1, len(pending))
         arrived = collections.deque()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        threads = [threading.Thread(target=self._worker, args=(t0,), daemon=True)
-                   for _ in range(self.workers)]
-        for th in threads:
-            th.start()
+        outstanding = {}
         build_stream = torch.cuda.Stream(device=self.device)
-        while pending or arrived:
-            now = time.perf_counter() - t0
-            while pending and pending[0].arrival <= now:
-                arrived.append(pending.popleft())
-            admitted_any = False
-            while arrived:
-                req = arrived[0]
-                need = footprint_estimate(req.n, req.m)
-                with self._lock:
-                    busy = self._in_use
-                if busy > 0 and busy + need > self.budget:
-                    break
-                arrived.popleft()
-                g = wbpr_build(req.n, req.m, req.src, req.dst, req.cap, req.s, req.t, self.layout,
-                               self.opts, build_stream)
-                req.footprint = max(need, wbpr_get_info(g)["device_bytes"])
-                req.admitted = time.perf_counter() - t0
-                with self._lock:
-                    self._in_use += req.footprint
-                    self._ready.append((req, g))
-                    self._lock.notify_all()
-                admitted_any = True
-            if not admitted_any:
-                with self._lock:
-                    wait = 0.0005 if not pending else max(0.0, min(0.002, pending[0].arrival - now))
-                    self._lock.wait(wait)
-        with self._lock:
-            self._stop = True
-            self._lock.notify_all()
-        for th in threads:
-            th.join()
+        # While the persistent kernel runs, device allocations must be
+        # stream-ordered (cudaMallocAsync, the library's own allocator): a
+        # cudaMalloc from a caching allocator growing its pool would wait for
+        # every stream, the server's included.
+        restore_torch = torch_allocator_enabled()
+        if restore_torch:
+            use_torch_allocator(False)
+        torch.cuda.synchronize()
+        srv = wbpr_server_start(self.opts)
+        t0 = time.perf_counter()
+        last_progress = t0
+        try:
+            while pending or arrived or outstanding:
+                now = time.perf_counter() - t0
+                if time.perf_counter() - last_progress > self.stall_s:
+                    raise RuntimeError(f"server made no progress for {self.stall_s} s")
+                while pending and pending[0].arrival <= now:
+                    arrived.append(pending.popleft())
+                # admission: build and publish while the footprint fits
+                while arrived and len(outstanding) < max_inflight:
+                    req = arrived[0]
+                    need = footprint_estimate(req.n, req.m)
+                    if outstanding and self.in_use + need > self.budget:
+                        break
+                    arrived.popleft()
+                    tb = time.perf_counter()
+                    g = wbpr_build(req.n, req.m, req.src, req.dst, req.cap, req.s, req.t, self.layout,
+                                   None, build_stream)
+                    req.build_ms = 1e3 * (time.perf_counter() - tb)
+                    req.footprint = max(need, wbpr_get_info(g)["device_bytes"])
+                    self.in_use += req.footprint
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    req.admitted = time.perf_counter() - t0
+                    outstanding[wbpr_server_submit(srv, g)] = (req, g)
+                # completions
+                done = []
+                for ticket, (req, g) in outstanding.items():
+                    try:
+                        v = wbpr_server_poll(srv, ticket)
+                    except Exception as exc:
+                        teams = self.opts.big_teams + self.opts.small_blocks
+                        exits = wbpr_server_team_exits(srv, teams)
+                        raise RuntimeError(
+                            f"request {req.rid} (ticket class {ticket >> 40}, index {ticket & ((1 << 40) - 1)}) "
+                            f"failed at t={time.perf_counter() - t0:.2f}s after admission at {req.admitted:.2f}s "
+                            f"(build {req.build_ms:.1f} ms); "
+                            f"team exit reasons {collections.Counter(exits)}") from exc
+                    if v is not None:
+                        req.value = v
+                        req.done = time.perf_counter() - t0
+                        done.append(ticket)
+                if done or not outstanding:
+                    last_progress = time.perf_counter()
+                for ticket in done:
+                    req, g = outstanding.pop(ticket)
+                    g.close()
+                    self.in_use -= req.footprint
+                if not done and not arrived and pending:
+                    time.sleep(max(0.0, min(0.0005, pending[0].arrival - (time.perf_counter() - t0))))
+        finally:
+            wbpr_server_stop(srv)
+            for req, g in outstanding.values():
+                g.close()
+            if restore_torch:
+                use_torch_allocator(True)
         return requests
 
 
