@@ -140,6 +140,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(ms: float, units: float, device=None):
+    """Whole-job figures over all ranks: the slowest rank's time and the sum
+    of the units every rank processed (replicas only: no data exchange)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(uu)
+    return float(tt.item()), float(uu.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -258,15 +272,7 @@ def run_gpu(args):
     barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-        aa = torch.tensor([arcs], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(aa)
-        arcs_all = float(aa.item())
-    else:
-        arcs_all = float(arcs)
+    ms, arcs_all = aggregate_ranks(ms, float(arcs), dev)
     value = arcs_all / (ms / 1e3)
 
     # time-to-maxflow with the graph resident (phase 1, value only), both layouts

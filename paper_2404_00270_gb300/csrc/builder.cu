@@ -4,8 +4,11 @@
 // (row u, col v, c) and (row v, col u, 0).  Sorting the half-entries by
 // (row, col) and merging equal keys gives one slot per neighbour pair with
 // cf0 = sum of the capacities u -> v; rows come out sorted by neighbour id,
-// which the binary-search backward lookup of §3.2 needs.  rev[a] is the
-// slot of the paired entry, found once by that binary search.
+// which the binary-search backward lookup of §3.2 needs.  The two
+// half-entries of one arc carry their positions through the sort, so they
+// land in mutually reverse slots: rev[] and arc2slot[] are scatters.
+// Keys pack (row, col) into 2 * bitlen(n) bits, so the radix sorts only make
+// as many passes as the vertex count needs.
 // RCSR (Fig. 2(c)): out rows = arcs sorted by (src, dst); in rows = the same
 // arcs sorted by (dst, src), each in entry keeping flow_idx, the out slot.
 // Sorting and scans use CUB (device radix sort / scan, header-only).
@@ -22,7 +25,7 @@ namespace {
 
 typedef unsigned long long u64;
 
-__global__ void validate_keys(long long m, int n, const int *src, const int *dst, const int *cap,
+__global__ void validate_keys(long long m, int n, int b, const int *src, const int *dst, const int *cap,
                               u64 *key, unsigned *val, int *bad, unsigned long long *nonloop)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -34,10 +37,10 @@ __global__ void validate_keys(long long m, int n, const int *src, const int *dst
             u = v = 0;
         }
         if (u != v) {
-            key[i] = ((u64)(unsigned)u << 32) | (unsigned)v;
+            key[i] = ((u64)(unsigned)u << b) | (unsigned)v;
             ++local;
         } else {
-            key[i] = (u64)(unsigned)n << 32;  // self-loops sort after every real arc
+            key[i] = (u64)(unsigned)n << b;  // self-loops sort after every real arc
         }
         val[i] = (unsigned)i;
     }
@@ -61,17 +64,18 @@ __global__ void scatter_prefix(long long mp, const unsigned *val, const int *pre
         prefix[val[j]] = pre_sorted[j];
 }
 
-__global__ void half_entries(long long mp, const u64 *key_sorted, const int *cap_sorted, u64 *key2,
-                             int *val2)
+// Half-entry 2j is arc j (in (src, dst) order) seen from its tail, 2j+1 the
+// same arc seen from its head; the sort carries these positions along.
+__global__ void half_entries(long long mp, int b, const u64 *key_sorted, u64 *key2, unsigned *pos2)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const u64 mask = (1ull << b) - 1;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride) {
         u64 k = key_sorted[j];
-        u64 rk = (k << 32) | (k >> 32);
         key2[2 * j] = k;
-        val2[2 * j] = cap_sorted[j];
-        key2[2 * j + 1] = rk;
-        val2[2 * j + 1] = 0;
+        pos2[2 * j] = (unsigned)(2 * j);
+        key2[2 * j + 1] = ((k & mask) << b) | (k >> b);
+        pos2[2 * j + 1] = (unsigned)(2 * j + 1);
     }
 }
 
@@ -82,21 +86,49 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
         head[j] = (j == 0 || key[j] != key[j - 1]) ? 1u : 0u;
 }
 
-// slot_of = inclusive scan of run heads (1-based slot numbers).
-__global__ void merge_runs(long long len, const u64 *key, const int *val, const unsigned *slot_of,
-                           u64 *ukey, int *col, long long *csum)
+// slot_of = inclusive scan of run heads (1-based slot numbers).  Merges equal
+// keys into one slot (capacity = sum over the arcs seen from their tail) and
+// records the slot of every half-entry position.
+__global__ void merge_runs(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
+                           const int *cap_sorted, u64 *ukey, int *col, long long *csum, unsigned *slot_by_pos)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const u64 mask = (1ull << b) - 1;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
-        unsigned a = slot_of[j] - 1;
-        u64 k = key[j];
+        const unsigned a = slot_of[j] - 1;
+        const u64 k = key[j];
         if (j == 0 || k != key[j - 1]) {
             ukey[a] = k;
-            col[a] = (int)(k & 0xffffffffu);
+            col[a] = (int)(k & mask);
         }
-        int c = val[j];
-        if (c) atomicAdd((u64 *)(csum + a), (u64)(long long)c);
+        const unsigned p = pos[j];
+        slot_by_pos[p] = a;
+        if ((p & 1u) == 0) {
+            const int c = cap_sorted[p >> 1];
+            if (c) atomicAdd((u64 *)(csum + a), (u64)(long long)c);
+        }
     }
+}
+
+// The two half-entries of arc j sit in mutually reverse slots; arc2slot of
+// the input arc is the slot of its tail-side half-entry.
+__global__ void pair_slots(long long mp, const unsigned *slot_by_pos, const unsigned *arc_of_sorted,
+                           unsigned *rev, unsigned *arc2slot)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride) {
+        const unsigned a = slot_by_pos[2 * j], r = slot_by_pos[2 * j + 1];
+        rev[a] = r;
+        rev[r] = a;
+        arc2slot[arc_of_sorted[j]] = a;
+    }
+}
+
+__global__ void pair_capacity_check(long long S, const int *cf0, const unsigned *rev, int *bad)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride)
+        if ((long long)cf0[a] + (long long)cf0[rev[a]] > 0x7fffffffLL) atomicOr(bad, 4);
 }
 
 __global__ void narrow_caps(long long S, const long long *csum, int *cf0, int *cf, int *bad)
@@ -132,29 +164,6 @@ __global__ void fill_i64(long long len, long long *p, long long x)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += stride) p[i] = x;
 }
 
-__device__ __forceinline__ long long lower_bound_col(const int *col, long long b, long long e, int key)
-{
-    while (b < e) {
-        long long mid = (b + e) >> 1;
-        if (col[mid] < key) b = mid + 1;
-        else e = mid;
-    }
-    return b;
-}
-
-__global__ void reverse_slots(long long S, const u64 *ukey, const int *col, const long long *off,
-                              const int *cf0, unsigned *rev, int *bad)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride) {
-        int u = (int)(ukey[a] >> 32);
-        int v = col[a];
-        long long r = lower_bound_col(col, off[v], off[v + 1], u);
-        rev[a] = (unsigned)r;
-        if ((long long)cf0[a] + (long long)cf0[r] > 0x7fffffffLL) atomicOr(bad, 4);
-    }
-}
-
 __global__ void max_degree_kernel(int n, const long long *off, const long long *in_off,
                                   unsigned long long *out)
 {
@@ -171,17 +180,7 @@ __global__ void max_degree_kernel(int n, const long long *off, const long long *
     if (threadIdx.x == 0 && mx) atomicMax(out, mx);
 }
 
-__global__ void arc_slots_bcsr(long long m, const int *src, const int *dst, const int *col,
-                               const long long *off, unsigned *arc2slot)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
-        int u = src[i], v = dst[i];
-        arc2slot[i] = (u == v) ? 0xffffffffu : (unsigned)lower_bound_col(col, off[u], off[u + 1], v);
-    }
-}
-
-__global__ void rcsr_out(long long mp, const unsigned *val, const int *dst, const int *cap,
+__global__ void rcsr_out(long long mp, int b, const unsigned *val, const int *dst, const int *cap,
                          const u64 *key_sorted, int *col, int *cf0, int *cf, unsigned *arc2slot,
                          u64 *key_in, unsigned *val_in)
 {
@@ -193,17 +192,17 @@ __global__ void rcsr_out(long long mp, const unsigned *val, const int *dst, cons
         cf[j] = cap[i];
         arc2slot[i] = (unsigned)j;
         u64 k = key_sorted[j];
-        key_in[j] = (k << 32) | (k >> 32);
+        key_in[j] = ((k & ((1ull << b) - 1)) << b) | (k >> b);
         val_in[j] = (unsigned)j;
     }
 }
 
-__global__ void rcsr_in(long long mp, const u64 *key_in_sorted, const unsigned *val_in_sorted,
+__global__ void rcsr_in(long long mp, int b, const u64 *key_in_sorted, const unsigned *val_in_sorted,
                         int *in_col, unsigned *flow_idx)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < mp; k += stride) {
-        in_col[k] = (int)(key_in_sorted[k] & 0xffffffffu);
+        in_col[k] = (int)(key_in_sorted[k] & ((1ull << b) - 1));
         flow_idx[k] = val_in_sorted[k];
     }
 }
@@ -299,8 +298,9 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
     BUILD_ALLOC(counter, unsigned long long, 4, pool);
     BUILD_CUDA(cudaMemsetAsync(bad, 0, 4 * sizeof(int), st));
     BUILD_CUDA(cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned long long), st));
+    const int kb = bitlen(n);  // bits of a vertex id in a packed (row, col) key
     if (m > 0) {
-        validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, src, dst, cap, key1, val1, bad, counter);
+        validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, src, dst, cap, key1, val1, bad, counter);
         BUILD_CUDA(cudaGetLastError());
     }
     int h_bad = 0;
@@ -311,7 +311,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
     if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
     const long long mp = (long long)h_nonloop;
     g->mprime = mp;
-    const int end_bit = 32 + bitlen(n);
+    const int end_bit = 2 * kb;
 
     // ---- sort arcs by (src, dst); CUB radix sort is stable ---------------------
     size_t temp_bytes = 0, need = 0;
@@ -361,24 +361,20 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         // ---- half entries, sorted and merged ------------------------------------
         const long long len = 2 * mp;
         u64 *k2, *k2b;
-        int *v2, *v2b;
+        unsigned *v2, *v2b;
         BUILD_ALLOC(k2, u64, len, pool);
         BUILD_ALLOC(k2b, u64, len, pool);
-        BUILD_ALLOC(v2, int, len, pool);
-        BUILD_ALLOC(v2b, int, len, pool);
+        BUILD_ALLOC(v2, unsigned, len, pool);
+        BUILD_ALLOC(v2b, unsigned, len, pool);
         if (mp > 0) {
-            half_entries<<<grid_for(mp), 256, 0, st>>>(mp, ks, cap_sorted, k2, v2);
+            half_entries<<<grid_for(mp), 256, 0, st>>>(mp, kb, ks, k2, v2);
             BUILD_CUDA(cudaGetLastError());
         }
-        pool.release(cap_sorted);
         pool.release(temp);
         temp = nullptr;
-        pool.release(key1);
-        pool.release(key1b);
-        pool.release(val1);
-        pool.release(val1b);
+        pool.release(key1 == ks ? key1b : key1);  // the sorted keys stay for nothing; vs stays
         cub::DoubleBuffer<u64> dk2(k2, k2b);
-        cub::DoubleBuffer<int> dv2(v2, v2b);
+        cub::DoubleBuffer<unsigned> dv2(v2, v2b);
         if (len > 0) {
             size_t nb = 0;
             BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk2, dv2, (int64_t)len, 0, end_bit, st));
@@ -388,7 +384,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             pool.release(t3);
         }
         u64 *k2s = dk2.Current();
-        int *v2s = dv2.Current();
+        unsigned *v2s = dv2.Current();
         unsigned *heads;
         BUILD_ALLOC(heads, unsigned, len, pool);
         unsigned S = 0;
@@ -407,31 +403,34 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         g->slots = S;
         u64 *ukey;
         long long *csum;
+        unsigned *slot_by_pos;
         BUILD_ALLOC(ukey, u64, S, pool);
         BUILD_ALLOC(csum, long long, S, pool);
+        BUILD_ALLOC(slot_by_pos, unsigned, len, pool);
         OWN_ALLOC(g->col, int, S);
         OWN_ALLOC(g->cf, int, S);
         OWN_ALLOC(g->cf0, int, S);
         OWN_ALLOC(g->rev, unsigned, S);
         OWN_ALLOC(g->cfb, int, S);
+        BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
         if (S > 0) {
             BUILD_CUDA(cudaMemsetAsync(csum, 0, sizeof(long long) * S, st));
-            merge_runs<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, heads, ukey, g->col, csum);
+            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cap_sorted, ukey, g->col, csum,
+                                                       slot_by_pos);
             BUILD_CUDA(cudaGetLastError());
             narrow_caps<<<grid_for(S), 256, 0, st>>>(S, csum, g->cf0, g->cf, bad);
             BUILD_CUDA(cudaGetLastError());
-            row_offsets<<<grid_for(S), 256, 0, st>>>(S, (int)n, ukey, 32, g->off);
+            row_offsets<<<grid_for(S), 256, 0, st>>>(S, (int)n, ukey, kb, g->off);
             BUILD_CUDA(cudaGetLastError());
-            reverse_slots<<<grid_for(S), 256, 0, st>>>(S, ukey, g->col, g->off, g->cf0, g->rev, bad);
+            pair_slots<<<grid_for(mp), 256, 0, st>>>(mp, slot_by_pos, vs, g->rev, g->arc2slot);
+            BUILD_CUDA(cudaGetLastError());
+            pair_capacity_check<<<grid_for(S), 256, 0, st>>>(S, g->cf0, g->rev, bad);
             BUILD_CUDA(cudaGetLastError());
         } else {
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
             BUILD_CUDA(cudaGetLastError());
         }
-        if (m > 0) {
-            arc_slots_bcsr<<<grid_for(m), 256, 0, st>>>(m, src, dst, g->col, g->off, g->arc2slot);
-            BUILD_CUDA(cudaGetLastError());
-        }
+        pool.release(cap_sorted);
         max_degree_kernel<<<grid_for(n), 256, 0, st>>>((int)n, g->off, nullptr, h_maxdeg_dev);
         BUILD_CUDA(cudaGetLastError());
     } else {
@@ -452,11 +451,11 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_ALLOC(vin, unsigned, mp, pool);
         BUILD_ALLOC(vinb, unsigned, mp, pool);
         if (mp > 0) {
-            rcsr_out<<<grid_for(mp), 256, 0, st>>>(mp, vs, dst, cap, ks, g->col, g->cf0, g->cf,
+            rcsr_out<<<grid_for(mp), 256, 0, st>>>(mp, kb, vs, dst, cap, ks, g->col, g->cf0, g->cf,
                                                    g->arc2slot, kin, vin);
             BUILD_CUDA(cudaGetLastError());
             BUILD_CUDA(cudaMemsetAsync(g->bf, 0, sizeof(int) * (size_t)mp, st));
-            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, ks, 32, g->off);
+            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, ks, kb, g->off);
             BUILD_CUDA(cudaGetLastError());
             cub::DoubleBuffer<u64> dki(kin, kinb);
             cub::DoubleBuffer<unsigned> dvi(vin, vinb);
@@ -466,9 +465,9 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             if (!t5) return set_error(WBPR_ENOMEM, "build: device allocation failed");
             BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t5, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
             pool.release(t5);
-            rcsr_in<<<grid_for(mp), 256, 0, st>>>(mp, dki.Current(), dvi.Current(), g->in_col, g->flow_idx);
+            rcsr_in<<<grid_for(mp), 256, 0, st>>>(mp, kb, dki.Current(), dvi.Current(), g->in_col, g->flow_idx);
             BUILD_CUDA(cudaGetLastError());
-            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, dki.Current(), 32, g->in_off);
+            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, dki.Current(), kb, g->in_off);
             BUILD_CUDA(cudaGetLastError());
         } else {
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);

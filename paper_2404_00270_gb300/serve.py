@@ -56,7 +56,7 @@ class Server:
     """Admission by footprint in front of the persistent server kernel."""
 
     def __init__(self, memory_budget: int, layout: int = WBPR_BCSR, big_slots: int = 1 << 15,
-                 team_blocks: int = 16, big_teams: int | None = None, small_blocks: int | None = None,
+                 team_blocks: int = 8, big_teams: int | None = None, small_blocks: int | None = None,
                  idle_ms: int = 60000, device=None):
         load()
         self.device = torch.device(device or "cuda", torch.cuda.current_device())
@@ -71,7 +71,7 @@ class Server:
         # leave on an SM)
         total = torch.cuda.get_device_properties(self.device).multi_processor_count
         if big_teams is None:
-            big_teams = max(1, total // 2 // team_blocks)
+            big_teams = max(1, (total * 3 // 5) // team_blocks)
         if small_blocks is None:
             small_blocks = max(1, total - big_teams * team_blocks)
         self.opts.team_blocks = team_blocks

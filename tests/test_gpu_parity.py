@@ -303,3 +303,17 @@ def test_time_balanced_relabel_same_results(ratio):
     for g in (W.rmat(12, 16, 21), W.grid(24, 24, 5)):
         src, dst, cap = g.numpy()
         check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
+
+
+def test_autotune_keeps_the_value():
+    from paper_2404_00270_gb300 import autotune
+    m = wb()
+    g = W.rmat(11, 16, 33)
+    src, dst, cap = g.numpy()
+    ref = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t, False, False)["value"]
+    cfg, ms, trials = autotune.autotune(g.n, g.m, src, dst, cap, g.s, g.t, limit=12, reps=1)
+    assert len(trials) == 12 and ms > 0
+    o = m.wbpr_default_options()
+    for k, v in cfg.items():
+        setattr(o, k, v)
+    check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
