@@ -62,7 +62,8 @@ class Options(ctypes.Structure):
                 ("warp_max_degree", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("barrier_timeout_ms", ctypes.c_int32), ("max_iterations", ctypes.c_int64),
                 ("trace", ctypes.c_int32), ("gr_ratio", ctypes.c_float),
-                ("batch_team", ctypes.c_int32), ("batch_big_slots", ctypes.c_int64)]
+                ("batch_team", ctypes.c_int32), ("batch_big_slots", ctypes.c_int64),
+                ("bottom_up", ctypes.c_int32), ("bottom_up_min", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -98,6 +98,8 @@ void wbpr_default_options(wbpr_options *o)
     o->gr_ratio = 1.0f;
     o->batch_team = 16;
     o->batch_big_slots = (int64_t)1 << 15;
+    o->bottom_up = 14;
+    o->bottom_up_min = 1024;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -141,6 +143,7 @@ static wbpr_status check_options(const wbpr_options *o)
     if (!(o->gr_ratio >= 0.f && o->gr_ratio < 1e6f)) return WBPR_EINVAL;
     if (o->batch_team < 1 || o->batch_team > 64 || (o->batch_team & (o->batch_team - 1))) return WBPR_EINVAL;
     if (o->batch_big_slots < 0) return WBPR_EINVAL;
+    if (o->bottom_up < 0 || o->bottom_up > (1 << 20) || o->bottom_up_min < 1) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -179,6 +182,8 @@ static wbpr_status alloc_state(wbpr_graph *g, cudaStream_t st)
     for (int a = 0; a < 2; ++a) {
         for (int k = 0; k < kClasses; ++k) STATE_ALLOC(g->q[a][k], int, n);
         STATE_ALLOC(g->hub_start[a], unsigned, n);
+        STATE_ALLOC(g->hub_chunk[a], unsigned,
+                    hub_chunk_entries(n, g->slots, g->layout == WBPR_BCSR ? kBCSR : kRCSR));
         STATE_ALLOC(g->hub_e0[a], long long, n);
         STATE_ALLOC(g->hub_rem[a], long long, n);
         STATE_ALLOC(g->hub_aux[a], unsigned long long, n);
@@ -399,6 +404,7 @@ Params make_params(wbpr_graph *g, int mode)
     for (int a = 0; a < 2; ++a) {
         for (int k = 0; k < kClasses; ++k) p.st.q[a][k] = g->q[a][k];
         p.st.hub_start[a] = g->hub_start[a];
+        p.st.hub_chunk[a] = g->hub_chunk[a];
         p.st.hub_e0[a] = g->hub_e0[a];
         p.st.hub_rem[a] = g->hub_rem[a];
         p.st.hub_aux[a] = g->hub_aux[a];
@@ -415,6 +421,8 @@ Params make_params(wbpr_graph *g, int mode)
     p.use_rev = g->layout == WBPR_BCSR ? g->opts.use_rev : 0;
     p.small_max = g->opts.small_max_degree;
     p.warp_max = g->opts.warp_max_degree;
+    p.bottom_up = g->opts.bottom_up;
+    p.bottom_up_min = g->opts.bottom_up_min;
     p.max_iterations = g->opts.max_iterations;
     p.timeout_ns = (unsigned long long)g->opts.barrier_timeout_ms * 1000000ull;
     if (g->opts.trace > 0) {
@@ -449,12 +457,13 @@ static wbpr_status launch_solver(wbpr_graph *g, cudaStream_t st, int mode, long 
     return WBPR_OK;
 }
 
+static_assert(sizeof(Ctl) <= 64 * sizeof(long long), "the host staging buffer holds the control block");
+
 // After a synchronised launch: read the status and counters.
 static wbpr_status collect(wbpr_graph *g, cudaStream_t st, bool accumulate)
 {
     long long *hp = g->pinned;
-    API_CUDA(cudaMemcpyAsync(hp, g->ctl, sizeof(Ctl) < 64 * sizeof(long long) ? sizeof(Ctl) : 64 * sizeof(long long),
-                             cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaMemcpyAsync(hp, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     API_CUDA(cudaStreamSynchronize(st));
     Ctl c;
     memcpy(&c, hp, sizeof(Ctl));

@@ -1,17 +1,20 @@
 // Graph builder: input arcs (COO, device) -> the residual layouts of §3.2.
 //
-// BCSR (Fig. 2(d)): every non-loop arc (u,v,c) contributes a half-entry
-// (row u, col v, c) and (row v, col u, 0).  Sorting the half-entries by
-// (row, col) and merging equal keys gives one slot per neighbour pair with
+// BCSR (Fig. 2(d)): every non-loop input arc i = (u,v,c) contributes two
+// half-entries, position 2i (row u, col v, capacity c) and position 2i + 1
+// (row v, col u, capacity 0).  One stable radix sort of the half-entries by
+// (row, col) and a merge of equal keys give one slot per neighbour pair with
 // cf0 = sum of the capacities u -> v; rows come out sorted by neighbour id,
-// which the binary-search backward lookup of §3.2 needs.  The two
-// half-entries of one arc carry their positions through the sort, so they
-// land in mutually reverse slots: rev[] and arc2slot[] are scatters.
-// Keys pack (row, col) into 2 * bitlen(n) bits, so the radix sorts only make
-// as many passes as the vertex count needs.
+// which the binary-search backward lookup of §3.2 needs.  The positions ride
+// through the sort, so the two half-entries of an arc land in mutually
+// reverse slots (rev[] and arc2slot[] are scatters), and duplicates of (u, v)
+// stay in input order inside their run (the edge-flow split's prefix is a
+// scan by key).
 // RCSR (Fig. 2(c)): out rows = arcs sorted by (src, dst); in rows = the same
 // arcs sorted by (dst, src), each in entry keeping flow_idx, the out slot.
-// Sorting and scans use CUB (device radix sort / scan, header-only).
+// Keys pack (row, col) into 2 * bitlen(n - 1) bits, so the radix sorts make
+// only as many passes as the vertex count needs.  Sorting and scans use CUB
+// (device radix sort / scan, header-only).
 #include <cub/cub.cuh>
 
 #include <stdint.h>
@@ -25,8 +28,8 @@ namespace {
 
 typedef unsigned long long u64;
 
-__global__ void validate_keys(long long m, int n, int b, const int *src, const int *dst, const int *cap,
-                              u64 *key, unsigned *val, int *bad, unsigned long long *nonloop)
+__global__ void validate_keys(long long m, int n, int b, u64 loop_key, const int *src, const int *dst,
+                              const int *cap, u64 *key, unsigned *val, int *bad, unsigned long long *nonloop)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned long long local = 0;
@@ -40,7 +43,7 @@ __global__ void validate_keys(long long m, int n, int b, const int *src, const i
             key[i] = ((u64)(unsigned)u << b) | (unsigned)v;
             ++local;
         } else {
-            key[i] = (u64)(unsigned)n << b;  // self-loops sort after every real arc
+            key[i] = loop_key;
         }
         val[i] = (unsigned)i;
     }
@@ -50,32 +53,53 @@ __global__ void validate_keys(long long m, int n, int b, const int *src, const i
     if (threadIdx.x == 0 && local) atomicAdd(nonloop, local);
 }
 
-__global__ void gather_caps(long long mp, const unsigned *val, const int *cap, int *out)
+// BCSR half-entries: position 2i is input arc i seen from its tail (row u,
+// col v), position 2i + 1 the same arc seen from its head (row v, col u).
+// The stable sort carries the positions along.
+__global__ void half_keys(long long m, int n, int b, u64 loop_key, const int *src, const int *dst, const int *cap,
+                          u64 *key2, unsigned *pos2, int *bad, unsigned long long *nonloop)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride)
-        out[j] = cap[val[j]];
+    unsigned long long local = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        int u = src[i], v = dst[i], c = cap[i];
+        if (u < 0 || u >= n || v < 0 || v >= n || c < 0) {
+            atomicOr(bad, 1);
+            u = v = 0;
+        }
+        if (u != v) {
+            key2[2 * i] = ((u64)(unsigned)u << b) | (unsigned)v;
+            key2[2 * i + 1] = ((u64)(unsigned)v << b) | (unsigned)u;
+            ++local;
+        } else {
+            key2[2 * i] = loop_key;
+            key2[2 * i + 1] = loop_key;
+        }
+        pos2[2 * i] = (unsigned)(2 * i);
+        pos2[2 * i + 1] = (unsigned)(2 * i + 1);
+    }
+    typedef cub::BlockReduce<unsigned long long, 256> Reduce;
+    __shared__ typename Reduce::TempStorage tmp;
+    local = Reduce(tmp).Sum(local);
+    if (threadIdx.x == 0 && local) atomicAdd(nonloop, local);
 }
 
-__global__ void scatter_prefix(long long mp, const unsigned *val, const int *pre_sorted, int *prefix)
+// Capacity of each sorted half-entry's arc on its tail side, 0 on its head side.
+__global__ void tail_caps(long long len, const unsigned *pos, const int *cap, int *out)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride)
-        prefix[val[j]] = pre_sorted[j];
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
+        const unsigned p = pos[j];
+        out[j] = (p & 1u) ? 0 : cap[p >> 1];
+    }
 }
 
-// Half-entry 2j is arc j (in (src, dst) order) seen from its tail, 2j+1 the
-// same arc seen from its head; the sort carries these positions along.
-__global__ void half_entries(long long mp, int b, const u64 *key_sorted, u64 *key2, unsigned *pos2)
+__global__ void scatter_prefix(long long len, const unsigned *pos, const int *pre, int *prefix)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const u64 mask = (1ull << b) - 1;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride) {
-        u64 k = key_sorted[j];
-        key2[2 * j] = k;
-        pos2[2 * j] = (unsigned)(2 * j);
-        key2[2 * j + 1] = ((k & mask) << b) | (k >> b);
-        pos2[2 * j + 1] = (unsigned)(2 * j + 1);
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
+        const unsigned p = pos[j];
+        if ((p & 1u) == 0) prefix[p >> 1] = pre[j];
     }
 }
 
@@ -90,7 +114,7 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
 // keys into one slot (capacity = sum over the arcs seen from their tail) and
 // records the slot of every half-entry position.
 __global__ void merge_runs(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
-                           const int *cap_sorted, u64 *ukey, int *col, long long *csum, unsigned *slot_by_pos)
+                           const int *cap, u64 *ukey, int *col, long long *csum, unsigned *slot_by_pos)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const u64 mask = (1ull << b) - 1;
@@ -104,23 +128,24 @@ __global__ void merge_runs(long long len, int b, const u64 *key, const unsigned 
         const unsigned p = pos[j];
         slot_by_pos[p] = a;
         if ((p & 1u) == 0) {
-            const int c = cap_sorted[p >> 1];
+            const int c = cap[p >> 1];
             if (c) atomicAdd((u64 *)(csum + a), (u64)(long long)c);
         }
     }
 }
 
-// The two half-entries of arc j sit in mutually reverse slots; arc2slot of
-// the input arc is the slot of its tail-side half-entry.
-__global__ void pair_slots(long long mp, const unsigned *slot_by_pos, const unsigned *arc_of_sorted,
+// The two half-entries of input arc i sit in mutually reverse slots;
+// arc2slot of the arc is the slot of its tail-side half-entry.
+__global__ void pair_slots(long long m, const int *src, const int *dst, const unsigned *slot_by_pos,
                            unsigned *rev, unsigned *arc2slot)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < mp; j += stride) {
-        const unsigned a = slot_by_pos[2 * j], r = slot_by_pos[2 * j + 1];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        if (src[i] == dst[i]) continue;  // self-loop: no slot
+        const unsigned a = slot_by_pos[2 * i], r = slot_by_pos[2 * i + 1];
         rev[a] = r;
         rev[r] = a;
-        arc2slot[arc_of_sorted[j]] = a;
+        arc2slot[i] = a;
     }
 }
 
@@ -285,106 +310,88 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
 {
     const long long n = g->n, m = g->m;
     Scratch pool(st);
-    // ---- validate and form (src, dst) keys ---------------------------------
-    u64 *key1, *key1b;
-    unsigned *val1, *val1b;
     int *bad;
     unsigned long long *counter;
-    BUILD_ALLOC(key1, u64, m, pool);
-    BUILD_ALLOC(key1b, u64, m, pool);
-    BUILD_ALLOC(val1, unsigned, m, pool);
-    BUILD_ALLOC(val1b, unsigned, m, pool);
     BUILD_ALLOC(bad, int, 4, pool);
     BUILD_ALLOC(counter, unsigned long long, 4, pool);
     BUILD_CUDA(cudaMemsetAsync(bad, 0, 4 * sizeof(int), st));
     BUILD_CUDA(cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned long long), st));
-    const int kb = bitlen(n);  // bits of a vertex id in a packed (row, col) key
-    if (m > 0) {
-        validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, src, dst, cap, key1, val1, bad, counter);
-        BUILD_CUDA(cudaGetLastError());
-    }
+    // Keys pack (row, col) into 2 * kb bits.  The all-ones key would be the
+    // self-loop (2^kb - 1, 2^kb - 1), so it can mark self-loops: they sort last.
+    const int kb = bitlen(n - 1);
+    const int end_bit = 2 * kb;
+    const u64 loop_key = (1ull << end_bit) - 1;
     int h_bad = 0;
     unsigned long long h_nonloop = 0;
-    BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-    BUILD_CUDA(cudaMemcpyAsync(&h_nonloop, counter, sizeof(h_nonloop), cudaMemcpyDeviceToHost, st));
-    BUILD_CUDA(cudaStreamSynchronize(st));
-    if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
-    const long long mp = (long long)h_nonloop;
-    g->mprime = mp;
-    const int end_bit = 2 * kb;
-
-    // ---- sort arcs by (src, dst); CUB radix sort is stable ---------------------
-    size_t temp_bytes = 0, need = 0;
-    cub::DoubleBuffer<u64> dk(key1, key1b);
-    cub::DoubleBuffer<unsigned> dv(val1, val1b);
-    if (m > 0) {
-        BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, need, dk, dv, (int64_t)m, 0, end_bit, st));
-        temp_bytes = need;
-    }
-    void *temp = nullptr;
-    if (temp_bytes) {
-        temp = pool.get(temp_bytes);
-        if (!temp) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-        BUILD_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, dk, dv, (int64_t)m, 0, end_bit, st));
-    }
-    u64 *ks = dk.Current();
-    unsigned *vs = dv.Current();
 
     OWN_ALLOC(g->arc2slot, unsigned, m);
     OWN_ALLOC(g->off, long long, n + 1);
     unsigned long long *h_maxdeg_dev = counter + 1;
+    BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
 
     if (g->layout == WBPR_BCSR) {
-        // ---- duplicate prefix (edge-flow split in input order) ------------------
-        OWN_ALLOC(g->prefix, int, m);
-        OWN_ALLOC(g->cap_in, int, m);
-        if (m > 0) BUILD_CUDA(cudaMemcpyAsync(g->cap_in, cap, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st));
-        BUILD_CUDA(cudaMemsetAsync(g->prefix, 0, sizeof(int) * (size_t)(m > 0 ? m : 1), st));
-        int *cap_sorted, *pre_sorted;
-        BUILD_ALLOC(cap_sorted, int, mp, pool);
-        BUILD_ALLOC(pre_sorted, int, mp, pool);
-        if (mp > 0) {
-            gather_caps<<<grid_for(mp), 256, 0, st>>>(mp, vs, cap, cap_sorted);
-            BUILD_CUDA(cudaGetLastError());
-            size_t nb = 0;
-            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, ks, cap_sorted, pre_sorted, (int64_t)mp,
-                                                          cuda::std::equal_to<>(), st));
-            void *t2 = pool.get(nb);
-            if (!t2) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, ks, cap_sorted, pre_sorted, (int64_t)mp,
-                                                          cuda::std::equal_to<>(), st));
-            pool.release(t2);
-            scatter_prefix<<<grid_for(mp), 256, 0, st>>>(mp, vs, pre_sorted, g->prefix);
-            BUILD_CUDA(cudaGetLastError());
-        }
-        pool.release(pre_sorted);
-        // ---- half entries, sorted and merged ------------------------------------
-        const long long len = 2 * mp;
+        // ---- both half-entries of every arc, one stable sort ---------------------
         u64 *k2, *k2b;
         unsigned *v2, *v2b;
-        BUILD_ALLOC(k2, u64, len, pool);
-        BUILD_ALLOC(k2b, u64, len, pool);
-        BUILD_ALLOC(v2, unsigned, len, pool);
-        BUILD_ALLOC(v2b, unsigned, len, pool);
-        if (mp > 0) {
-            half_entries<<<grid_for(mp), 256, 0, st>>>(mp, kb, ks, k2, v2);
+        BUILD_ALLOC(k2, u64, 2 * m, pool);
+        BUILD_ALLOC(k2b, u64, 2 * m, pool);
+        BUILD_ALLOC(v2, unsigned, 2 * m, pool);
+        BUILD_ALLOC(v2b, unsigned, 2 * m, pool);
+        if (m > 0) {
+            half_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, loop_key, src, dst, cap, k2, v2, bad, counter);
             BUILD_CUDA(cudaGetLastError());
         }
-        pool.release(temp);
-        temp = nullptr;
-        pool.release(key1 == ks ? key1b : key1);  // the sorted keys stay for nothing; vs stays
+        BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaMemcpyAsync(&h_nonloop, counter, sizeof(h_nonloop), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaStreamSynchronize(st));
+        if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
+        const long long mp = (long long)h_nonloop;
+        g->mprime = mp;
         cub::DoubleBuffer<u64> dk2(k2, k2b);
         cub::DoubleBuffer<unsigned> dv2(v2, v2b);
-        if (len > 0) {
+        if (m > 0) {
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk2, dv2, (int64_t)len, 0, end_bit, st));
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk2, dv2, (int64_t)(2 * m), 0, end_bit, st));
             void *t3 = pool.get(nb);
             if (!t3) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t3, nb, dk2, dv2, (int64_t)len, 0, end_bit, st));
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t3, nb, dk2, dv2, (int64_t)(2 * m), 0, end_bit, st));
             pool.release(t3);
         }
         u64 *k2s = dk2.Current();
         unsigned *v2s = dv2.Current();
+        pool.release(k2s == k2 ? k2b : k2);
+        pool.release(v2s == v2 ? v2b : v2);
+        const long long len = 2 * mp;  // the self-loops' entries sort after these
+
+        // ---- duplicate prefix (edge-flow split in input order) ------------------
+        // The sort is stable and positions grow with the input order, so the
+        // tail-side half-entries of duplicates of (u, v) sit in input order in
+        // one run: an exclusive sum by key over their capacities.
+        OWN_ALLOC(g->prefix, int, m);
+        OWN_ALLOC(g->cap_in, int, m);
+        if (m > 0) BUILD_CUDA(cudaMemcpyAsync(g->cap_in, cap, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st));
+        BUILD_CUDA(cudaMemsetAsync(g->prefix, 0, sizeof(int) * (size_t)(m > 0 ? m : 1), st));
+        if (len > 0) {
+            int *tail_cap, *pre;
+            BUILD_ALLOC(tail_cap, int, len, pool);
+            BUILD_ALLOC(pre, int, len, pool);
+            tail_caps<<<grid_for(len), 256, 0, st>>>(len, v2s, cap, tail_cap);
+            BUILD_CUDA(cudaGetLastError());
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, k2s, tail_cap, pre, (int64_t)len,
+                                                          cuda::std::equal_to<>(), st));
+            void *t2 = pool.get(nb);
+            if (!t2) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, k2s, tail_cap, pre, (int64_t)len,
+                                                          cuda::std::equal_to<>(), st));
+            pool.release(t2);
+            scatter_prefix<<<grid_for(len), 256, 0, st>>>(len, v2s, pre, g->prefix);
+            BUILD_CUDA(cudaGetLastError());
+            pool.release(pre);
+            pool.release(tail_cap);
+        }
+
+        // ---- merge runs into slots ------------------------------------------------
         unsigned *heads;
         BUILD_ALLOC(heads, unsigned, len, pool);
         unsigned S = 0;
@@ -406,23 +413,21 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         unsigned *slot_by_pos;
         BUILD_ALLOC(ukey, u64, S, pool);
         BUILD_ALLOC(csum, long long, S, pool);
-        BUILD_ALLOC(slot_by_pos, unsigned, len, pool);
+        BUILD_ALLOC(slot_by_pos, unsigned, 2 * m, pool);
         OWN_ALLOC(g->col, int, S);
         OWN_ALLOC(g->cf, int, S);
         OWN_ALLOC(g->cf0, int, S);
         OWN_ALLOC(g->rev, unsigned, S);
         OWN_ALLOC(g->cfb, int, S);
-        BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
         if (S > 0) {
             BUILD_CUDA(cudaMemsetAsync(csum, 0, sizeof(long long) * S, st));
-            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cap_sorted, ukey, g->col, csum,
-                                                       slot_by_pos);
+            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cap, ukey, g->col, csum, slot_by_pos);
             BUILD_CUDA(cudaGetLastError());
             narrow_caps<<<grid_for(S), 256, 0, st>>>(S, csum, g->cf0, g->cf, bad);
             BUILD_CUDA(cudaGetLastError());
             row_offsets<<<grid_for(S), 256, 0, st>>>(S, (int)n, ukey, kb, g->off);
             BUILD_CUDA(cudaGetLastError());
-            pair_slots<<<grid_for(mp), 256, 0, st>>>(mp, slot_by_pos, vs, g->rev, g->arc2slot);
+            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->rev, g->arc2slot);
             BUILD_CUDA(cudaGetLastError());
             pair_capacity_check<<<grid_for(S), 256, 0, st>>>(S, g->cf0, g->rev, bad);
             BUILD_CUDA(cudaGetLastError());
@@ -430,11 +435,41 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
             BUILD_CUDA(cudaGetLastError());
         }
-        pool.release(cap_sorted);
         max_degree_kernel<<<grid_for(n), 256, 0, st>>>((int)n, g->off, nullptr, h_maxdeg_dev);
         BUILD_CUDA(cudaGetLastError());
     } else {
-        // ---- RCSR -----------------------------------------------------------------
+        // ---- RCSR: arcs sorted by (src, dst); CUB radix sort is stable ----------------
+        u64 *key1, *key1b;
+        unsigned *val1, *val1b;
+        BUILD_ALLOC(key1, u64, m, pool);
+        BUILD_ALLOC(key1b, u64, m, pool);
+        BUILD_ALLOC(val1, unsigned, m, pool);
+        BUILD_ALLOC(val1b, unsigned, m, pool);
+        if (m > 0) {
+            validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, loop_key, src, dst, cap, key1, val1, bad,
+                                                       counter);
+            BUILD_CUDA(cudaGetLastError());
+        }
+        BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaMemcpyAsync(&h_nonloop, counter, sizeof(h_nonloop), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaStreamSynchronize(st));
+        if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
+        const long long mp = (long long)h_nonloop;
+        g->mprime = mp;
+        cub::DoubleBuffer<u64> dk(key1, key1b);
+        cub::DoubleBuffer<unsigned> dv(val1, val1b);
+        if (m > 0) {
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk, dv, (int64_t)m, 0, end_bit, st));
+            void *t1 = pool.get(nb);
+            if (!t1) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t1, nb, dk, dv, (int64_t)m, 0, end_bit, st));
+            pool.release(t1);
+        }
+        u64 *ks = dk.Current();
+        unsigned *vs = dv.Current();
+        pool.release(ks == key1 ? key1b : key1);
+        pool.release(vs == val1 ? val1b : val1);
         g->slots = mp;
         OWN_ALLOC(g->col, int, mp);
         OWN_ALLOC(g->cf, int, mp);
@@ -443,7 +478,6 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         OWN_ALLOC(g->in_off, long long, n + 1);
         OWN_ALLOC(g->in_col, int, mp);
         OWN_ALLOC(g->flow_idx, unsigned, mp);
-        BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
         u64 *kin, *kinb;
         unsigned *vin, *vinb;
         BUILD_ALLOC(kin, u64, mp, pool);

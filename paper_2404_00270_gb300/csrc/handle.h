@@ -64,6 +64,7 @@ struct wbpr_graph {
     int *count = nullptr;
     int *q[2][wbpr::kClasses] = {{nullptr}};
     unsigned *hub_start[2] = {nullptr, nullptr};
+    unsigned *hub_chunk[2] = {nullptr, nullptr};  // chunk id -> hub queue position
     long long *hub_e0[2] = {nullptr, nullptr};
     long long *hub_rem[2] = {nullptr, nullptr};
     unsigned long long *hub_aux[2] = {nullptr, nullptr};

@@ -36,7 +36,9 @@ constexpr size_t kOffDead = align256(kOffH + 4 * kMaxN);
 constexpr size_t kOffCount = align256(kOffDead + kMaxN);
 constexpr size_t kOffQ = align256(kOffCount + 4 * (kMaxN + 1));
 constexpr size_t kOffHubStart = align256(kOffQ + 6 * 4 * kMaxN);
-constexpr size_t kOffHubE0 = align256(kOffHubStart + 2 * 4 * kMaxN);
+constexpr long long kMaxChunks = kMaxN + kMaxSlots / kChunk + 1;  // hub_chunk_entries() for BCSR
+constexpr size_t kOffHubChunk = align256(kOffHubStart + 2 * 4 * kMaxN);
+constexpr size_t kOffHubE0 = align256(kOffHubChunk + 2 * 4 * kMaxChunks);
 constexpr size_t kOffHubRem = align256(kOffHubE0 + 2 * 8 * kMaxN);
 constexpr size_t kOffHubAux = align256(kOffHubRem + 2 * 8 * kMaxN);
 constexpr size_t kOffHubDone = align256(kOffHubAux + 2 * 8 * kMaxN);
@@ -131,6 +133,7 @@ extern "C" wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32
     for (int a = 0; a < 2; ++a) {
         for (int k = 0; k < kClasses; ++k) p.st.q[a][k] = (int *)(base + kOffQ) + (size_t)(a * kClasses + k) * kMaxN;
         p.st.hub_start[a] = (unsigned *)(base + kOffHubStart) + (size_t)a * kMaxN;
+        p.st.hub_chunk[a] = (unsigned *)(base + kOffHubChunk) + (size_t)a * kMaxChunks;
         p.st.hub_e0[a] = (long long *)(base + kOffHubE0) + (size_t)a * kMaxN;
         p.st.hub_rem[a] = (long long *)(base + kOffHubRem) + (size_t)a * kMaxN;
         p.st.hub_aux[a] = (unsigned long long *)(base + kOffHubAux) + (size_t)a * kMaxN;
@@ -147,6 +150,8 @@ extern "C" wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32
     p.multi_push = o.multi_push;
     p.small_max = o.small_max_degree;
     p.warp_max = o.warp_max_degree;
+    p.bottom_up = o.bottom_up;
+    p.bottom_up_min = o.bottom_up_min;
     p.max_iterations = o.max_iterations;
     p.timeout_ns = (unsigned long long)o.barrier_timeout_ms * 1000000ull;
 

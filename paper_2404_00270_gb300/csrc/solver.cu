@@ -37,6 +37,7 @@
 
 #include "wbpr_internal.cuh"
 
+
 namespace wbpr {
 namespace {
 
@@ -78,8 +79,12 @@ __device__ __forceinline__ u64 tile_min(u64 x)
     return x;
 }
 
+constexpr int kBuVerts = 4;  // vertices per thread per bottom-up pass
+
 struct Smem {
     int qbuf[kClasses][kQueueCap];
+    int dfr[kBlock * kBuVerts];  // bottom-up BFS: rows deferred to a warp (front) or the block (back)
+    unsigned ndfr_lo, ndfr_hi;
     unsigned qcnt[kClasses];
     unsigned qbase[kClasses];
     u64 red[kWarps];
@@ -219,8 +224,9 @@ __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
 // ---------------------------------------------------------------------------
 // Hub class: a vertex whose residual list is longer than warp_max is split
 // into chunks of kChunk entries.  One 64-bit atomic gives it both its queue
-// position and the id of its first chunk, so chunk ids grow with the
-// position and a chunk id maps back to its hub by binary search.
+// position and the id of its first chunk; the appender then records the
+// position under each of its chunk ids, so a block that takes a chunk id
+// finds its hub with one load.
 // ---------------------------------------------------------------------------
 constexpr u64 kChunkMask = (1ull << 40) - 1;
 
@@ -233,10 +239,13 @@ __device__ __forceinline__ void hub_append(Ctx &c, int slot3, int set, int v, lo
                                            long long ev)
 {
     const StateDev &st = c.P.st;
-    const u64 old = atomicAdd(&st.ctl->hub_pack[slot3], (1ull << 40) | hub_chunks(deg));
+    const unsigned nch = hub_chunks(deg);
+    const u64 old = atomicAdd(&st.ctl->hub_pack[slot3], (1ull << 40) | nch);
     const unsigned pos = (unsigned)(old >> 40);
+    const unsigned first = (unsigned)(old & kChunkMask);
     st.q[set][2][pos] = v;
-    st.hub_start[set][pos] = (unsigned)(old & kChunkMask);
+    st.hub_start[set][pos] = first;
+    for (unsigned j = 0; j < nch; ++j) st.hub_chunk[set][first + j] = pos;
     if (pr) {
         st.hub_e0[set][pos] = ev;
         st.hub_rem[set][pos] = ev;
@@ -260,12 +269,7 @@ __device__ bool grab_chunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunk
         const unsigned id = atomicAdd(&c.P.st.ctl->q_grab[s3], 1u);
         if (id < nchunks) {
             const unsigned *start = c.P.st.hub_start[set];
-            unsigned lo = 0, hi = nh;  // start[lo] <= id < start[hi]
-            while (hi - lo > 1) {
-                unsigned mid = (lo + hi) >> 1;
-                if (__ldcg(start + mid) <= id) lo = mid;
-                else hi = mid;
-            }
+            const unsigned lo = __ldcg(c.P.st.hub_chunk[set] + id);  // start[lo] <= id < start[lo + 1]
             const unsigned s0 = __ldcg(start + lo);
             const unsigned s1 = lo + 1 < nh ? __ldcg(start + lo + 1) : nchunks;
             c.sm.hub_pos = lo;
@@ -1135,6 +1139,184 @@ __device__ void bfs_level(Ctx &c, int val)
     if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
 }
 
+// ---------------------------------------------------------------------------
+// Bottom-up level of the backward BFS (direction-optimising BFS, Beamer,
+// Asanovic and Patterson, SC 2012).  Instead of scanning the frontier's rows,
+// every unvisited vertex v scans its own row for a residual arc v -> w into
+// the frontier (h[w] == val - 1) and stops at the first one.  It visits
+// exactly the vertices a top-down level visits, with the same value, so the
+// distances are unchanged; only the entries read differ.  Only v's owner
+// writes h[v], so no claim is needed.  Rows of up to kBuThread entries are
+// scanned by one thread (kBuVerts vertices per thread, 4 entries per step),
+// longer rows by a warp, hub rows by the whole block.
+// ---------------------------------------------------------------------------
+constexpr int kBuThread = 32;
+constexpr int kBuStep = 4;
+
+// Residual arc v -> w over entry k of v's list (w returned).
+template <int L>
+__device__ __forceinline__ int bu_res(const GraphDev &g, long long k, bool in, int &w)
+{
+    if (L == kBCSR || !in) {
+        w = __ldg(g.col + k);
+        return __ldcg(g.cf + k);
+    }
+    w = __ldg(g.in_col + k);  // in slot of v: arc w -> v; residual v -> w is its flow
+    return __ldcg(g.bf + __ldg(g.flow_idx + k));
+}
+
+template <int L>
+__device__ __forceinline__ void bu_found(Ctx &c, int v, long long deg, int val, int nset, int n3)
+{
+    __stcg(c.P.st.h + v, val);
+    const int cls = classify(c.P, deg);
+    if (cls == 2) hub_append(c, n3, nset, v, deg, false, 0);
+    else q_append(c, n3, nset, cls, v);
+}
+
+
+// Scan W-lane groups of NB entries of v's row starting at row index r0 + sl;
+// true if one of them is a residual arc into the frontier.
+template <int L, int W, int NB>
+__device__ __forceinline__ bool bu_scan(const Params &P, long long ob, long long dout, long long ib,
+                                        long long deg, long long r0, int sl, int want)
+{
+    int w[NB], r[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const long long rr = r0 + sl + (long long)q * W;
+        r[q] = 0;
+        w[q] = 0;
+        if (rr < deg) {
+            bool in;
+            const long long k = row_slot<L>(ob, dout, ib, rr, in);
+            r[q] = bu_res<L>(P.g, k, in, w[q]);
+        }
+    }
+    bool hit = false;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) hit |= r[q] > 0 && __ldcg(P.st.h + w[q]) == want;
+    return hit;
+}
+
+template <int L>
+__device__ void bfs_level_bu(Ctx &c, int val)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int gen = c.gen, n3 = (gen + 1) % 3, nset = (gen + 1) & 1;
+    const int want = val - 1;
+    const long long n = g.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    reset_rotating(c, gen);
+    long long scanned = 0;
+    const long long span = (long long)kBlock * kBuVerts;
+    if (threadIdx.x == 0) {
+        c.sm.ndfr_lo = 0;
+        c.sm.ndfr_hi = 0;
+    }
+    __syncthreads();
+    for (long long base = (long long)c.bid * span; base < n; base += (long long)c.nblk * span) {
+        int v[kBuVerts];
+        long long ob[kBuVerts], dout[kBuVerts], ib[kBuVerts], deg[kBuVerts];
+        bool live[kBuVerts];
+#pragma unroll
+        for (int i = 0; i < kBuVerts; ++i) {
+            v[i] = (int)(base + (long long)i * kBlock + threadIdx.x);
+            live[i] = v[i] < n && __ldcg(P.st.h + v[i]) == kUnvisited;
+        }
+#pragma unroll
+        for (int i = 0; i < kBuVerts; ++i) {
+            ob[i] = dout[i] = ib[i] = deg[i] = 0;
+            if (live[i]) {
+                ob[i] = __ldg(g.off + v[i]);
+                dout[i] = __ldg(g.off + v[i] + 1) - ob[i];
+                deg[i] = dout[i];
+                if (L == kRCSR) {
+                    ib[i] = __ldg(g.in_off + v[i]);
+                    deg[i] += __ldg(g.in_off + v[i] + 1) - ib[i];
+                }
+                if (deg[i] == 0) {
+                    live[i] = false;
+                } else if (deg[i] > kBuThread) {
+                    live[i] = false;
+                    if (classify(P, deg[i]) == 2) c.sm.dfr[span - 1 - atomicAdd(&c.sm.ndfr_hi, 1u)] = v[i];
+                    else c.sm.dfr[atomicAdd(&c.sm.ndfr_lo, 1u)] = v[i];
+                }
+            }
+        }
+        for (long long r0 = 0; r0 < kBuThread; r0 += kBuStep) {
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < kBuVerts; ++i) any |= live[i];
+            if (!any) break;
+            bool hit[kBuVerts];
+#pragma unroll
+            for (int i = 0; i < kBuVerts; ++i) {
+                hit[i] = false;
+                if (live[i]) hit[i] = bu_scan<L, 1, kBuStep>(P, ob[i], dout[i], ib[i], deg[i], r0, 0, want);
+            }
+#pragma unroll
+            for (int i = 0; i < kBuVerts; ++i) {
+                if (!live[i]) continue;
+                const long long left = deg[i] - r0;
+                scanned += left < kBuStep ? left : kBuStep;
+                if (hit[i]) bu_found<L>(c, v[i], deg[i], val, nset, n3);
+                if (hit[i] || left <= kBuStep) live[i] = false;
+            }
+        }
+        __syncthreads();
+        // rows longer than kBuThread: one warp each
+        const unsigned nlo = c.sm.ndfr_lo, nhi = c.sm.ndfr_hi;
+        for (unsigned i = warp; i < nlo; i += kWarps) {
+            const int u = c.sm.dfr[i];
+            const long long o = __ldg(g.off + u), dO = __ldg(g.off + u + 1) - o;
+            long long ii = 0, d = dO;
+            if (L == kRCSR) {
+                ii = __ldg(g.in_off + u);
+                d += __ldg(g.in_off + u + 1) - ii;
+            }
+            for (long long r0 = 0; r0 < d; r0 += 32 * kBuStep) {
+                const bool h1 = bu_scan<L, 32, kBuStep>(P, o, dO, ii, d, r0, lane, want);
+                if (lane == 0) scanned += d - r0 < 32 * kBuStep ? d - r0 : 32 * kBuStep;
+                if (__any_sync(kFull, h1)) {
+                    if (lane == 0) bu_found<L>(c, u, d, val, nset, n3);
+                    break;
+                }
+            }
+        }
+        // hub rows: the whole block, kBlock * kBuStep entries per step
+        for (unsigned i = 0; i < nhi; ++i) {
+            const int u = c.sm.dfr[span - 1 - i];
+            const long long o = __ldg(g.off + u), dO = __ldg(g.off + u + 1) - o;
+            long long ii = 0, d = dO;
+            if (L == kRCSR) {
+                ii = __ldg(g.in_off + u);
+                d += __ldg(g.in_off + u + 1) - ii;
+            }
+            for (long long r0 = 0; r0 < d; r0 += (long long)kBlock * kBuStep) {
+                const bool h1 = bu_scan<L, kBlock, kBuStep>(P, o, dO, ii, d, r0, threadIdx.x, want);
+                if (threadIdx.x == 0) scanned += d - r0 < kBlock * kBuStep ? d - r0 : kBlock * kBuStep;
+                if (__syncthreads_or(h1)) {
+                    if (threadIdx.x == 0) bu_found<L>(c, u, d, val, nset, n3);
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        const bool flush = c.sm.qcnt[0] > (unsigned)(kQueueCap / 2) || c.sm.qcnt[1] > (unsigned)(kQueueCap / 2);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            c.sm.ndfr_lo = 0;
+            c.sm.ndfr_hi = 0;
+        }
+        if (flush) q_flush(c, n3, nset);  // block-uniform; starts with a barrier
+        __syncthreads();
+    }
+    q_flush(c, n3, nset);
+    if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
+}
+
 // Seed a BFS: generation `gen` holds the single vertex v.
 template <int L>
 __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
@@ -1144,8 +1326,10 @@ __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
         const int cls = classify(c.P, d);
         c.P.st.q[gen & 1][cls][0] = v;
         if (cls == 2) {
+            const unsigned nch = hub_chunks(d);
             c.P.st.hub_start[gen & 1][0] = 0;
-            c.P.st.ctl->hub_pack[gen % 3] = (1ull << 40) | hub_chunks(d);
+            for (unsigned j = 0; j < nch; ++j) c.P.st.hub_chunk[gen & 1][j] = 0;
+            c.P.st.ctl->hub_pack[gen % 3] = (1ull << 40) | nch;
         } else {
             c.P.st.ctl->q_count[gen % 3][cls] = 1;
         }
@@ -1177,11 +1361,26 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
     }
     seed_queue<L>(c, c.gen, target);
     if (!grid_sync(c, 10)) return false;
+    // Direction choice (after Beamer et al.): a level runs bottom-up when its
+    // frontier, times bottom_up, reaches the vertices not yet visited (an
+    // over-estimate: written-off vertices count as unvisited) and holds at
+    // least bottom_up_min vertices.  Uniform over the team: every block reads
+    // the same counters after the barrier.  Phase 1 only: there the vertices
+    // that cannot reach t are written off and skipped by later global
+    // relabels, while in phase 2 the vertices that cannot reach s would scan
+    // their whole rows in every bottom-up level of every global relabel.
+    long long seen = 0;
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
         if (gap && c.bid == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
-        bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
+        seen += tot;
+        const bool bu_mode = phase1 && P.bottom_up > 0 && tot >= (unsigned)P.bottom_up_min &&
+                             (long long)tot * P.bottom_up >= (long long)n - seen;
+        if (bu_mode)
+            bfs_level_bu<L>(c, base + level + 1);
+        else
+            bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
         if (!grid_sync(c, 11)) return false;
         c.gen++;
     }
@@ -1375,7 +1574,7 @@ __device__ bool min_cut(Ctx &c)
 
 // One whole solve (the modes in P.mode) by the calling team of blocks.
 template <int L, int SW>
-__device__ void solve_instance(Ctx &c)
+__device__ __forceinline__ void solve_instance(Ctx &c)
 {
     const Params &P = c.P;
     Smem &sm = c.sm;

@@ -84,6 +84,13 @@ struct GraphDev {
     const unsigned *flow_idx;   // RCSR
 };
 
+// Upper bound on the hub chunks of one queue generation: every hub has at
+// most deg / kChunk + 1 chunks and the degrees sum to the residual-list entries.
+inline long long hub_chunk_entries(long long n, long long slots, int layout_tag)
+{
+    return n + (layout_tag == kRCSR ? 2 * slots : slots) / kChunk + 1;
+}
+
 struct StateDev {
     long long *e;
     int *h;
@@ -94,6 +101,7 @@ struct StateDev {
     // compaction, excess not yet taken by a chunk, min key / min residual height,
     // chunks finished
     unsigned *hub_start[2];
+    unsigned *hub_chunk[2];     // chunk id -> hub queue position; hub_chunk_entries(n, slots, L) each
     long long *hub_e0[2];
     long long *hub_rem[2];
     unsigned long long *hub_aux[2];
@@ -124,6 +132,9 @@ struct Params {
     int multi_push;
     int small_max;
     int warp_max;
+    int bottom_up;               // > 0: phase-1 bottom-up BFS levels when frontier * bottom_up >=
+                                 //      unvisited vertices
+    int bottom_up_min;           //      and frontier >= bottom_up_min
     long long max_iterations;
     unsigned long long timeout_ns;
     unsigned char *source_side;  // kModeCut output (device, n bytes) or null

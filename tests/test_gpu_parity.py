@@ -147,15 +147,26 @@ def test_builder_arrays_bit_exact(layout):
         G.close()
 
 
+BU_MODES = {"top-down": (0, 1024), "default": (14, 1024), "bottom-up": (1 << 20, 1)}
+
+
+def _bu_options(m, mode):
+    o = m.wbpr_default_options()
+    o.bottom_up, o.bottom_up_min = BU_MODES[mode]
+    return o
+
+
+@pytest.mark.parametrize("bu", list(BU_MODES))
 @pytest.mark.parametrize("layout", LAYOUTS)
-def test_preflow_and_global_relabel_stages(layout):
+def test_preflow_and_global_relabel_stages(layout, bu):
     """Preflow state and global-relabel heights (BFS distances to t over the
-    residual arcs of the exported snapshot, s excluded) bit-exact."""
+    residual arcs of the exported snapshot, s excluded) bit-exact, with the
+    BFS levels top-down, bottom-up, or switched by frontier size."""
     m = wb()
     g = W.rmat(11, 8, 9)
     src, dst, cap = g.numpy()
     n, s, t = g.n, g.s, g.t
-    G = m.wbpr_build(n, src.size, src, dst, cap, s, t, layout_code(layout))
+    G = m.wbpr_build(n, src.size, src, dst, cap, s, t, layout_code(layout), _bu_options(m, bu))
     m.wbpr_run_stage(G, 1)   # preflow
     h = m.wbpr_export(G, "height")
     e = m.wbpr_export(G, "excess")
@@ -303,6 +314,23 @@ def test_time_balanced_relabel_same_results(ratio):
     for g in (W.rmat(12, 16, 21), W.grid(24, 24, 5)):
         src, dst, cap = g.numpy()
         check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
+
+
+@pytest.mark.parametrize("bu", list(BU_MODES))
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_bottom_up_bfs_same_results(layout, bu):
+    """Value, cut and canonical side do not depend on the BFS direction, on
+    graphs whose middle levels are large (R-MAT, bipartite) and on a grid
+    (long thin levels); hub rows are scanned by whole blocks bottom-up."""
+    m = wb()
+    o = _bu_options(m, bu)
+    for g in (W.rmat(14, 16, 41), W.bipartite_zipf(4096, 4096, 43), W.grid(40, 40, 47)):
+        src, dst, cap = g.numpy()
+        check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o)
+    o.warp_max_degree = 16   # rows over 16 entries scanned by whole blocks
+    g = W.rmat(12, 16, 45)
+    src, dst, cap = g.numpy()
+    check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o)
 
 
 def test_autotune_keeps_the_value():
