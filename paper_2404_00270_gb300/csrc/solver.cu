@@ -1338,10 +1338,12 @@ __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
 
 // Global relabel (§2.2): heights = base + BFS distance to `target` over
 // residual arcs, never through `excluded`; unreachable vertices get
-// `unreach`.  Phase 1 writes off the excess of newly unreachable vertices
-// (Excess_total -= e(v), once per vertex) and rebuilds the gap counts.
+// `unreach` and a mark in dead[] that later global relabels of the phase
+// skip.  Phase 1 writes off the excess of newly unreachable vertices
+// (Excess_total -= e(v), once per vertex) and rebuilds the gap counts; in
+// phase 2 an unreachable vertex holds no excess (all excess can return to s).
 template <int L, int SW>
-__device__ bool global_relabel(Ctx &c, bool phase1)
+__device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false)
 {
     const Params &P = c.P;
     const GraphDev &g = P.g;
@@ -1356,26 +1358,28 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
     for (long long v = c.bid * kBlock + threadIdx.x; v <= n; v += stride) {
         if (gap) __stcg(P.st.count + v, 0);
         if (v == n || v == excluded) continue;
-        if (phase1 && P.st.dead[v]) continue;
+        if (first_of_phase2) P.st.dead[v] = 0;  // phase 1's marks mean "cannot reach t"
+        else if (P.st.dead[v]) continue;
         __stcg(P.st.h + v, v == target ? base : kUnvisited);
     }
     seed_queue<L>(c, c.gen, target);
     if (!grid_sync(c, 10)) return false;
     // Direction choice (after Beamer et al.): a level runs bottom-up when its
     // frontier, times bottom_up, reaches the vertices not yet visited (an
-    // over-estimate: written-off vertices count as unvisited) and holds at
-    // least bottom_up_min vertices.  Uniform over the team: every block reads
-    // the same counters after the barrier.  Phase 1 only: there the vertices
-    // that cannot reach t are written off and skipped by later global
-    // relabels, while in phase 2 the vertices that cannot reach s would scan
-    // their whole rows in every bottom-up level of every global relabel.
+    // over-estimate: marked vertices count as unvisited) and holds at least
+    // bottom_up_min vertices.  Uniform over the team: every block reads the
+    // same counters after the barrier.  Vertices that cannot reach the target
+    // are marked (dead[]) and skipped by the later global relabels of the
+    // phase, so bottom-up levels do not rescan their rows: no residual path
+    // to the target can appear for them, because no push ever enters a
+    // vertex at the height cap.
     long long seen = 0;
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
         if (gap && c.bid == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
         seen += tot;
-        const bool bu_mode = phase1 && P.bottom_up > 0 && tot >= (unsigned)P.bottom_up_min &&
+        const bool bu_mode = P.bottom_up > 0 && tot >= (unsigned)P.bottom_up_min &&
                              (long long)tot * P.bottom_up >= (long long)n - seen;
         if (bu_mode)
             bfs_level_bu<L>(c, base + level + 1);
@@ -1389,9 +1393,9 @@ __device__ bool global_relabel(Ctx &c, bool phase1)
         if (v == excluded) continue;
         if (__ldcg(P.st.h + v) == kUnvisited) {
             __stcg(P.st.h + v, unreach);
-            if (phase1 && !P.st.dead[v]) {
+            if (!P.st.dead[v]) {
                 P.st.dead[v] = 1;
-                wo += __ldcg(P.st.e + v);
+                if (phase1) wo += __ldcg(P.st.e + v);
             }
         }
     }
@@ -1455,7 +1459,7 @@ __device__ bool run_phase(Ctx &c, bool phase1, long long *it_total)
 {
     const Params &P = c.P;
     Ctl *ctl = P.st.ctl;
-    if (!global_relabel<L, SW>(c, phase1)) return false;
+    if (!global_relabel<L, SW>(c, phase1, !phase1)) return false;
     int idle_rounds = 0;
     for (;;) {
         const long long es = __ldcg(P.st.e + P.g.s), et = __ldcg(P.st.e + P.g.t);

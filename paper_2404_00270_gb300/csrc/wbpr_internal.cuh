@@ -132,7 +132,7 @@ struct Params {
     int multi_push;
     int small_max;
     int warp_max;
-    int bottom_up;               // > 0: phase-1 bottom-up BFS levels when frontier * bottom_up >=
+    int bottom_up;               // > 0: bottom-up BFS levels when frontier * bottom_up >=
                                  //      unvisited vertices
     int bottom_up_min;           //      and frontier >= bottom_up_min
     long long max_iterations;
