@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 METRIC = "residual arcs scanned/s (R-MAT 20 max-flow + min-cut, BCSR)"
 UNIT = "arcs/s"
 
+# The library's own kernels per step: the BCSR build (half_keys, tail_caps,
+# scatter_prefix, run_heads, merge_runs, narrow_caps, row_offsets, pair_slots,
+# pair_capacity_check, max_degree_kernel), solve_kernel for the flow and for
+# the cut, and edge_flow_kernel.  CUB's sort and scan kernels come on top.
+LAUNCHES_PER_STEP = 13
+
 # Algorithmic bytes per unit of the BCSR solver (each unit is counted by the
 # kernel itself, see wbpr_get_stats).
 B_ENTRY = 12          # BCSR entry scanned: col 4 + cf 4 + h[col] 4
@@ -335,14 +341,16 @@ def run_gpu(args):
         "config": {"workload": f"rmat{args.scale}-maxflow-mincut", "scale": args.scale, "edge_factor": 16,
                    "n": n, "m": m, "s": s, "t": t, "layout": "bcsr+rev",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (COO 193 MB, BCSR 503 MB per step)",
+                   "l2": (f"inputs larger than L2 (COO {12 * m / 1e6:.0f} MB"
+                          + (f", BCSR handle {breakdown['bcsr']['device_bytes'] / 1e6:.0f} MB" if breakdown else "")
+                          + " per step)"),
                    "flow_value": value_seen,
                    "time_to_maxflow_ms": breakdown["bcsr"]["time_to_maxflow_ms"] if breakdown else None,
                    "layouts": breakdown},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel",
                      "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"},
-        "gpu_launches": args.steps * 14,
+        "gpu_launches": args.steps * LAUNCHES_PER_STEP,
         "clocks": clocks,
         "e2e": e2e,
     }
