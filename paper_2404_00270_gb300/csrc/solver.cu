@@ -893,38 +893,51 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
     const long long chunk = ((long long)n + c.nblk - 1) / c.nblk;
     const long long v0 = chunk * c.bid;
     const long long v1 = v0 + chunk < n ? v0 + chunk : n;
-    long long nact = 0, lifted = 0;
-    for (long long base = v0; base < v1; base += kBlock) {
-        long long v = base + threadIdx.x;
-        if (v < v1) {
-            int hv = __ldcg(P.st.h + v);
-            if (gap != kUnvisited && hv > gap && hv < n && v != s) {
-                hv = n;
+    // kAvqVerts vertices per thread per step, their loads issued together
+    // (heights, then excesses, then row offsets of the active ones).
+    constexpr int kAvqVerts = 4;
+    long long nact = 0;
+    for (long long base = v0; base < v1; base += (long long)kBlock * kAvqVerts) {
+        int hv[kAvqVerts];
+        long long ev[kAvqVerts], d[kAvqVerts];
+#pragma unroll
+        for (int i = 0; i < kAvqVerts; ++i) {
+            const long long v = base + (long long)i * kBlock + threadIdx.x;
+            hv[i] = v < v1 ? __ldcg(P.st.h + v) : hcap;
+        }
+#pragma unroll
+        for (int i = 0; i < kAvqVerts; ++i) {
+            const long long v = base + (long long)i * kBlock + threadIdx.x;
+            if (v < v1 && gap != kUnvisited && hv[i] > gap && hv[i] < n && v != s) {
+                hv[i] = n;
                 __stcg(P.st.h + v, n);
-                ++lifted;
             }
-            if (v != s && v != t && hv < hcap) {
-                const long long ev = __ldcg(P.st.e + v);
-                if (ev > 0) {
-                    const long long d = degree<L>(g, (int)v);
-                    const int cls = classify(P, d);
-                    if (cls == 2) hub_append(c, s3, set, (int)v, d, true, ev);
-                    else q_append(c, s3, set, cls, (int)v);
-                    ++nact;
-                }
-            }
+            ev[i] = (v < v1 && v != s && v != t && hv[i] < hcap) ? __ldcg(P.st.e + v) : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kAvqVerts; ++i) {
+            const long long v = base + (long long)i * kBlock + threadIdx.x;
+            d[i] = ev[i] > 0 ? degree<L>(g, (int)v) : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kAvqVerts; ++i) {
+            if (ev[i] <= 0) continue;
+            const int v = (int)(base + (long long)i * kBlock + threadIdx.x);
+            const int cls = classify(P, d[i]);
+            if (cls == 2) hub_append(c, s3, set, v, d[i], true, ev[i]);
+            else q_append(c, s3, set, cls, v);
+            ++nact;
         }
         __syncthreads();
         unsigned mx = c.sm.qcnt[0];
         if (c.sm.qcnt[1] > mx) mx = c.sm.qcnt[1];
         __syncthreads();  // every thread has read the counts before new appends
-        if (mx > (unsigned)(kQueueCap - kBlock)) q_flush(c, s3, set);
+        if (mx > (unsigned)(kQueueCap - kBlock * kAvqVerts)) q_flush(c, s3, set);
     }
     q_flush(c, s3, set);
     if (nact) atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)nact);
     if (c.bid == 0 && threadIdx.x == 0 && gap != kUnvisited)
         atomicAdd((unsigned long long *)&c.sm.stats[kStatGaps], 1ull);
-    (void)lifted;
 }
 
 // ---------------------------------------------------------------------------
@@ -932,7 +945,7 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
 //   kBfsBackward: from `target`, visit v when the residual arc v -> w exists
 //                 (w = frontier vertex); h[v] = level value (CAS on kUnvisited)
 //   kBfsForward:  from s, visit v when the residual arc w -> v exists; marks in
-//                 count[] (CAS 0 -> 1)
+//                 count[] (CAS 0 -> level value; s holds 1)
 // ---------------------------------------------------------------------------
 enum { kBfsBackward = 0, kBfsForward = 1 };
 
@@ -971,7 +984,7 @@ __device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int 
         fresh = __ldcg(h + v) == kUnvisited && atomicCAS(h + v, kUnvisited, val) == kUnvisited;
     } else {
         int *mark = P.st.count;
-        fresh = __ldcg(mark + v) == 0 && atomicCAS(mark + v, 0, 1) == 0;
+        fresh = __ldcg(mark + v) == 0 && atomicCAS(mark + v, 0, val) == 0;
     }
     if (fresh) {
         const long long d = degree<L>(P.g, v);
@@ -1140,35 +1153,55 @@ __device__ void bfs_level(Ctx &c, int val)
 }
 
 // ---------------------------------------------------------------------------
-// Bottom-up level of the backward BFS (direction-optimising BFS, Beamer,
-// Asanovic and Patterson, SC 2012).  Instead of scanning the frontier's rows,
-// every unvisited vertex v scans its own row for a residual arc v -> w into
-// the frontier (h[w] == val - 1) and stops at the first one.  It visits
-// exactly the vertices a top-down level visits, with the same value, so the
-// distances are unchanged; only the entries read differ.  Only v's owner
-// writes h[v], so no claim is needed.  Rows of up to kBuThread entries are
+// Bottom-up level of a BFS (direction-optimising BFS, Beamer, Asanovic and
+// Patterson, SC 2012).  Instead of scanning the frontier's rows, every
+// unvisited vertex v scans its own row for a residual arc into the frontier
+// (v -> w for the backward BFS of the global relabel, w -> v for the forward
+// BFS of the cut; w in the frontier when its level value is val - 1) and
+// stops at the first one.  It visits exactly the vertices a top-down level
+// visits, with the same value, so the distances are unchanged; only the
+// entries read differ.  Only v's owner writes v's level, so no claim is
+// needed.  Rows of up to kBuThread entries are
 // scanned by one thread (kBuVerts vertices per thread, 4 entries per step),
 // longer rows by a warp, hub rows by the whole block.
 // ---------------------------------------------------------------------------
 constexpr int kBuThread = 32;
 constexpr int kBuStep = 4;
 
-// Residual arc v -> w over entry k of v's list (w returned).
-template <int L>
+// Over entry k of v's list (neighbour w returned): the residual capacity of
+// v -> w (backward BFS) or of w -> v (forward BFS).
+template <int L, int DIR>
 __device__ __forceinline__ int bu_res(const GraphDev &g, long long k, bool in, int &w)
 {
-    if (L == kBCSR || !in) {
+    if (L == kBCSR) {
         w = __ldg(g.col + k);
-        return __ldcg(g.cf + k);
+        return DIR == kBfsBackward ? __ldcg(g.cf + k) : __ldcg(g.cfb + k);
     }
-    w = __ldg(g.in_col + k);  // in slot of v: arc w -> v; residual v -> w is its flow
-    return __ldcg(g.bf + __ldg(g.flow_idx + k));
+    if (!in) {  // out slot of v: arc v -> w; its reverse residual is its flow
+        w = __ldg(g.col + k);
+        return DIR == kBfsBackward ? __ldcg(g.cf + k) : __ldcg(g.bf + k);
+    }
+    w = __ldg(g.in_col + k);  // in slot of v: arc w -> v, out slot j
+    const unsigned j = __ldg(g.flow_idx + k);
+    return DIR == kBfsBackward ? __ldcg(g.bf + j) : __ldcg(g.cf + j);
 }
 
-template <int L>
+// The level array of a BFS direction: heights (backward) or cut marks.
+template <int DIR>
+__device__ __forceinline__ int *bfs_levels(const Params &P)
+{
+    return DIR == kBfsBackward ? P.st.h : P.st.count;
+}
+template <int DIR>
+__device__ __forceinline__ int bfs_unvisited()
+{
+    return DIR == kBfsBackward ? kUnvisited : 0;
+}
+
+template <int L, int DIR>
 __device__ __forceinline__ void bu_found(Ctx &c, int v, long long deg, int val, int nset, int n3)
 {
-    __stcg(c.P.st.h + v, val);
+    __stcg(bfs_levels<DIR>(c.P) + v, val);
     const int cls = classify(c.P, deg);
     if (cls == 2) hub_append(c, n3, nset, v, deg, false, 0);
     else q_append(c, n3, nset, cls, v);
@@ -1177,7 +1210,7 @@ __device__ __forceinline__ void bu_found(Ctx &c, int v, long long deg, int val, 
 
 // Scan W-lane groups of NB entries of v's row starting at row index r0 + sl;
 // true if one of them is a residual arc into the frontier.
-template <int L, int W, int NB>
+template <int L, int DIR, int W, int NB>
 __device__ __forceinline__ bool bu_scan(const Params &P, long long ob, long long dout, long long ib,
                                         long long deg, long long r0, int sl, int want)
 {
@@ -1190,16 +1223,17 @@ __device__ __forceinline__ bool bu_scan(const Params &P, long long ob, long long
         if (rr < deg) {
             bool in;
             const long long k = row_slot<L>(ob, dout, ib, rr, in);
-            r[q] = bu_res<L>(P.g, k, in, w[q]);
+            r[q] = bu_res<L, DIR>(P.g, k, in, w[q]);
         }
     }
+    const int *lvl = bfs_levels<DIR>(P);
     bool hit = false;
 #pragma unroll
-    for (int q = 0; q < NB; ++q) hit |= r[q] > 0 && __ldcg(P.st.h + w[q]) == want;
+    for (int q = 0; q < NB; ++q) hit |= r[q] > 0 && __ldcg(lvl + w[q]) == want;
     return hit;
 }
 
-template <int L>
+template <int L, int DIR>
 __device__ void bfs_level_bu(Ctx &c, int val)
 {
     const Params &P = c.P;
@@ -1223,7 +1257,7 @@ __device__ void bfs_level_bu(Ctx &c, int val)
 #pragma unroll
         for (int i = 0; i < kBuVerts; ++i) {
             v[i] = (int)(base + (long long)i * kBlock + threadIdx.x);
-            live[i] = v[i] < n && __ldcg(P.st.h + v[i]) == kUnvisited;
+            live[i] = v[i] < n && __ldcg(bfs_levels<DIR>(P) + v[i]) == bfs_unvisited<DIR>();
         }
 #pragma unroll
         for (int i = 0; i < kBuVerts; ++i) {
@@ -1254,14 +1288,14 @@ __device__ void bfs_level_bu(Ctx &c, int val)
 #pragma unroll
             for (int i = 0; i < kBuVerts; ++i) {
                 hit[i] = false;
-                if (live[i]) hit[i] = bu_scan<L, 1, kBuStep>(P, ob[i], dout[i], ib[i], deg[i], r0, 0, want);
+                if (live[i]) hit[i] = bu_scan<L, DIR, 1, kBuStep>(P, ob[i], dout[i], ib[i], deg[i], r0, 0, want);
             }
 #pragma unroll
             for (int i = 0; i < kBuVerts; ++i) {
                 if (!live[i]) continue;
                 const long long left = deg[i] - r0;
                 scanned += left < kBuStep ? left : kBuStep;
-                if (hit[i]) bu_found<L>(c, v[i], deg[i], val, nset, n3);
+                if (hit[i]) bu_found<L, DIR>(c, v[i], deg[i], val, nset, n3);
                 if (hit[i] || left <= kBuStep) live[i] = false;
             }
         }
@@ -1277,10 +1311,10 @@ __device__ void bfs_level_bu(Ctx &c, int val)
                 d += __ldg(g.in_off + u + 1) - ii;
             }
             for (long long r0 = 0; r0 < d; r0 += 32 * kBuStep) {
-                const bool h1 = bu_scan<L, 32, kBuStep>(P, o, dO, ii, d, r0, lane, want);
+                const bool h1 = bu_scan<L, DIR, 32, kBuStep>(P, o, dO, ii, d, r0, lane, want);
                 if (lane == 0) scanned += d - r0 < 32 * kBuStep ? d - r0 : 32 * kBuStep;
                 if (__any_sync(kFull, h1)) {
-                    if (lane == 0) bu_found<L>(c, u, d, val, nset, n3);
+                    if (lane == 0) bu_found<L, DIR>(c, u, d, val, nset, n3);
                     break;
                 }
             }
@@ -1295,10 +1329,10 @@ __device__ void bfs_level_bu(Ctx &c, int val)
                 d += __ldg(g.in_off + u + 1) - ii;
             }
             for (long long r0 = 0; r0 < d; r0 += (long long)kBlock * kBuStep) {
-                const bool h1 = bu_scan<L, kBlock, kBuStep>(P, o, dO, ii, d, r0, threadIdx.x, want);
+                const bool h1 = bu_scan<L, DIR, kBlock, kBuStep>(P, o, dO, ii, d, r0, threadIdx.x, want);
                 if (threadIdx.x == 0) scanned += d - r0 < kBlock * kBuStep ? d - r0 : kBlock * kBuStep;
                 if (__syncthreads_or(h1)) {
-                    if (threadIdx.x == 0) bu_found<L>(c, u, d, val, nset, n3);
+                    if (threadIdx.x == 0) bu_found<L, DIR>(c, u, d, val, nset, n3);
                     break;
                 }
             }
@@ -1315,6 +1349,115 @@ __device__ void bfs_level_bu(Ctx &c, int val)
     }
     q_flush(c, n3, nset);
     if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
+}
+
+// Capacity of the out-arcs from the marked side (mark != 0) to the rest,
+// initial capacities; this thread's share (valid once it returns true).
+// Rows of up to kBuThread entries are summed by one thread (kBuVerts vertices
+// at once).  Longer rows are queued in the next (empty) queue generation and,
+// after a barrier, taken across the grid: a warp per row, hub rows by chunks
+// of whole blocks.  R-MAT places its long rows at low ids, so rows handled by
+// the block that found them would all land on a few blocks.
+template <int L>
+__device__ bool cut_capacity(Ctx &c, long long &sum)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int *mark = P.st.count;
+    const long long n = g.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long span = (long long)kBlock * kBuVerts;
+    const int n3 = (c.gen + 1) % 3, nset = (c.gen + 1) & 1;  // generation c.gen + 1 is empty
+    sum = 0;
+    for (long long base = (long long)c.bid * span; base < n; base += (long long)c.nblk * span) {
+        long long ob[kBuVerts], deg[kBuVerts];
+        bool live[kBuVerts];
+#pragma unroll
+        for (int i = 0; i < kBuVerts; ++i) {
+            const long long v = base + (long long)i * kBlock + threadIdx.x;
+            live[i] = v < n && __ldcg(mark + v) != 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kBuVerts; ++i) {
+            ob[i] = deg[i] = 0;
+            if (live[i]) {
+                const long long v = base + (long long)i * kBlock + threadIdx.x;
+                ob[i] = __ldg(g.off + v);
+                deg[i] = __ldg(g.off + v + 1) - ob[i];
+                if (deg[i] > kBuThread) {
+                    live[i] = false;
+                    if (classify(P, deg[i]) == 2) hub_append(c, n3, nset, (int)v, deg[i], false, 0);
+                    else q_append(c, n3, nset, 1, (int)v);
+                }
+            }
+        }
+        for (long long r0 = 0; r0 < kBuThread; r0 += kBuStep) {
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < kBuVerts; ++i) any |= live[i] && r0 < deg[i];
+            if (!any) break;
+            int w[kBuVerts][kBuStep], cap[kBuVerts][kBuStep];
+#pragma unroll
+            for (int i = 0; i < kBuVerts; ++i)
+#pragma unroll
+                for (int q = 0; q < kBuStep; ++q) {
+                    const bool ok = live[i] && r0 + q < deg[i];
+                    w[i][q] = ok ? __ldg(g.col + ob[i] + r0 + q) : 0;
+                    cap[i][q] = ok ? __ldg(g.cf0 + ob[i] + r0 + q) : 0;
+                }
+#pragma unroll
+            for (int i = 0; i < kBuVerts; ++i)
+#pragma unroll
+                for (int q = 0; q < kBuStep; ++q)
+                    if (cap[i][q] && !__ldcg(mark + w[i][q])) sum += cap[i][q];
+        }
+    }
+    q_flush(c, n3, nset);
+    if (!grid_sync(c, 33)) return false;
+    // rows longer than kBuThread: one warp each, taken across the grid
+    {
+        const unsigned nmed = __ldcg(&P.st.ctl->q_count[n3][1]);
+        const int *q1 = P.st.q[nset][1];
+        for (unsigned i = (unsigned)(c.bid * kWarps + warp); i < nmed; i += c.nblk * kWarps) {
+            const int u = __ldcg(q1 + i);
+            const long long b = __ldg(g.off + u), e = __ldg(g.off + u + 1);
+            for (long long k0 = b; k0 < e; k0 += 32 * kBuStep) {
+                int w[kBuStep], cap[kBuStep];
+#pragma unroll
+                for (int q = 0; q < kBuStep; ++q) {
+                    const long long k = k0 + q * 32 + lane;
+                    w[q] = k < e ? __ldg(g.col + k) : 0;
+                    cap[q] = k < e ? __ldg(g.cf0 + k) : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < kBuStep; ++q)
+                    if (cap[q] && !__ldcg(mark + w[q])) sum += cap[q];
+            }
+        }
+    }
+
+    const u64 hp = __ldcg(&P.st.ctl->hub_pack[n3]);
+    const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
+    unsigned pos, j, nch;
+    if (nchunks) {
+        while (grab_chunk(c, n3, nset, nh, nchunks, pos, j, nch)) {
+            const int u = __ldcg(P.st.q[nset][2] + pos);
+            const long long b = __ldg(g.off + u), e = __ldg(g.off + u + 1);
+            const long long r0 = b + (long long)j * kChunk, r1 = e < r0 + kChunk ? e : r0 + kChunk;
+            constexpr int NB = kChunk / kBlock;
+            int w[NB], cap[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const long long k = r0 + (long long)q * kBlock + threadIdx.x;
+                w[q] = k < r1 ? __ldg(g.col + k) : 0;
+                cap[q] = k < r1 ? __ldg(g.cf0 + k) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (cap[q] && !__ldcg(mark + w[q])) sum += cap[q];
+        }
+    }
+    return true;
 }
 
 // Seed a BFS: generation `gen` holds the single vertex v.
@@ -1382,7 +1525,7 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         const bool bu_mode = P.bottom_up > 0 && tot >= (unsigned)P.bottom_up_min &&
                              (long long)tot * P.bottom_up >= (long long)n - seen;
         if (bu_mode)
-            bfs_level_bu<L>(c, base + level + 1);
+            bfs_level_bu<L, kBfsBackward>(c, base + level + 1);
         else
             bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
         if (!grid_sync(c, 11)) return false;
@@ -1540,28 +1683,27 @@ __device__ bool min_cut(Ctx &c)
     const int n = g.n;
     const long long stride = (long long)c.nblk * kBlock;
     const long long tid = c.bid * kBlock + threadIdx.x;
-    int *mark = P.st.count;
+    int *mark = P.st.count;  // 0 = not reached, else BFS level + 1
     for (long long v = tid; v <= n; v += stride) __stcg(mark + v, v == g.s ? 1 : 0);
     seed_queue<L>(c, c.gen, g.s);
     if (!grid_sync(c, 30)) return false;
-    for (;;) {
+    // Forward BFS from s, bottom-up on large frontiers (the forward residual
+    // w -> v of an entry of v's row needs cfb in BCSR).
+    const bool bu_ok = P.bottom_up > 0 && (L == kRCSR || g.cfb != nullptr);
+    long long seen = 0;
+    for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
-        bfs_level<L, kBfsForward, SW>(c, 1);
+        seen += tot;
+        if (bu_ok && tot >= (unsigned)P.bottom_up_min && (long long)tot * P.bottom_up >= (long long)n - seen)
+            bfs_level_bu<L, kBfsForward>(c, level + 2);
+        else
+            bfs_level<L, kBfsForward, SW>(c, level + 2);
         if (!grid_sync(c, 31)) return false;
         c.gen++;
     }
-    // cut capacity: arcs from the marked side to the rest (initial capacities)
-    const int lane = threadIdx.x & 31;
-    const long long gw = (c.bid * kBlock + threadIdx.x) >> 5;
-    const long long nw = stride >> 5;
     long long sum = 0;
-    for (long long u = gw; u < n; u += nw) {
-        if (!__ldcg(mark + u)) continue;
-        long long b = __ldg(g.off + u), e = __ldg(g.off + u + 1);
-        for (long long k = b + lane; k < e; k += 32)
-            if (!__ldcg(mark + __ldg(g.col + k))) sum += __ldg(g.cf0 + k);
-    }
+    if (!cut_capacity<L>(c, sum)) return false;
     long long bs = block_sum(c, sum);
     if (threadIdx.x == 0 && bs) atomicAdd((u64 *)&P.st.ctl->cut_value, (u64)bs);
     if (P.source_side)
