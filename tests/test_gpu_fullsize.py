@@ -74,11 +74,14 @@ def test_rmat26_certificate():
     g = W.rmat(26, 16, 4, cap_lo=1, cap_hi=10000, device="cuda:0")
     m = wb()
     G = m.wbpr_build(g.n, g.m, g.src, g.dst, g.cap, g.s, g.t, layout_code("bcsr"))
+    from bench import algorithmic_bytes
     for _ in range(2):   # phase 1 only, for the record (run with -s to see it)
         v1 = m.wbpr_maxflow(G)
         st = m.wbpr_get_stats(G)
+        ab = algorithmic_bytes(st, g.n)
         print(f"R-MAT 26 phase 1: value {v1}, {st['solve_ms']:.1f} ms, {st['iterations']} iterations, "
-              f"{st['global_relabels']} global relabels, handle {m.wbpr_get_info(G)['device_bytes'] / 1e9:.1f} GB")
+              f"{st['global_relabels']} global relabels, algorithmic bytes {ab / 1e9:.1f} GB "
+              f"({ab / (st['solve_ms'] * 1e6):.0f} GB/s), handle {m.wbpr_get_info(G)['device_bytes'] / 1e9:.1f} GB")
     G.close()
     value, cut, flow, side = _solve(g, "bcsr")
     assert value == cut == v1
