@@ -37,10 +37,10 @@ METRIC = "residual arcs scanned/s (R-MAT 20 max-flow + min-cut, BCSR)"
 UNIT = "arcs/s"
 
 # The library's own kernels per step: the BCSR build (half_keys, tail_caps,
-# scatter_prefix, run_heads, merge_runs, narrow_caps, row_offsets, pair_slots,
-# pair_capacity_check, max_degree_kernel), solve_kernel for the flow and for
-# the cut, and edge_flow_kernel.  CUB's sort and scan kernels come on top.
-LAUNCHES_PER_STEP = 13
+# scatter_prefix, run_heads, merge_runs, pair_slots, max_degree_kernel),
+# solve_kernel for the flow and for the cut, and edge_flow_kernel.  CUB's
+# sort and scan kernels come on top.
+LAUNCHES_PER_STEP = 10
 
 # Algorithmic bytes per unit of the BCSR solver (each unit is counted by the
 # kernel itself, see wbpr_get_stats).

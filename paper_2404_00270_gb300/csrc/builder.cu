@@ -110,34 +110,51 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
         head[j] = (j == 0 || key[j] != key[j - 1]) ? 1u : 0u;
 }
 
-// slot_of = inclusive scan of run heads (1-based slot numbers).  Merges equal
-// keys into one slot (capacity = sum over the arcs seen from their tail) and
-// records the slot of every half-entry position.
-__global__ void merge_runs(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
-                           const int *cap, u64 *ukey, int *col, long long *csum, unsigned *slot_by_pos)
+// slot_of = inclusive scan of run heads (1-based slot numbers).  Every
+// half-entry records its slot; the head of each run (one neighbour pair seen
+// from one side) writes the slot's column, sums the capacities of the run's
+// tail-side half-entries into cf0 / cf (flag 2 on int32 overflow), and writes
+// the offsets of the rows that start at its slot (rows with no slot take the
+// next row's start).  Runs are short: one per (u, v), as long as the number
+// of duplicate arcs between u and v.
+__global__ void merge_runs(long long len, int b, int n, const u64 *key, const unsigned *pos, const unsigned *slot_of,
+                           const int *cap, long long S, int *col, int *cf0, int *cf, long long *off,
+                           unsigned *slot_by_pos, int *bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const u64 mask = (1ull << b) - 1;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
         const unsigned a = slot_of[j] - 1;
         const u64 k = key[j];
-        if (j == 0 || k != key[j - 1]) {
-            ukey[a] = k;
-            col[a] = (int)(k & mask);
+        slot_by_pos[pos[j]] = a;
+        const u64 kp = j == 0 ? ~0ull : key[j - 1];
+        if (k == kp) continue;
+        col[a] = (int)(k & mask);
+        long long sum = 0;
+        for (long long i = j; i < len && key[i] == k; ++i) {
+            const unsigned p = pos[i];
+            if ((p & 1u) == 0) sum += cap[p >> 1];
         }
-        const unsigned p = pos[j];
-        slot_by_pos[p] = a;
-        if ((p & 1u) == 0) {
-            const int c = cap[p >> 1];
-            if (c) atomicAdd((u64 *)(csum + a), (u64)(long long)c);
+        if (sum > 0x7fffffffLL) {
+            atomicOr(bad, 2);
+            sum = 0;
         }
+        cf0[a] = (int)sum;
+        cf[a] = (int)sum;
+        const long long r = (long long)(k >> b);
+        const long long rp = j == 0 ? -1 : (long long)(kp >> b);
+        for (long long v = rp + 1; v <= r; ++v) off[v] = a;
+        if ((long long)a == S - 1)
+            for (long long v = r + 1; v <= n; ++v) off[v] = S;
     }
 }
 
 // The two half-entries of input arc i sit in mutually reverse slots;
-// arc2slot of the arc is the slot of its tail-side half-entry.
+// arc2slot of the arc is the slot of its tail-side half-entry.  The pair's
+// capacities must fit int32 together (flag 4), since a push moves residual
+// capacity from one slot to the other.
 __global__ void pair_slots(long long m, const int *src, const int *dst, const unsigned *slot_by_pos,
-                           unsigned *rev, unsigned *arc2slot)
+                           const int *cf0, unsigned *rev, unsigned *arc2slot, int *bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
@@ -146,27 +163,7 @@ __global__ void pair_slots(long long m, const int *src, const int *dst, const un
         rev[a] = r;
         rev[r] = a;
         arc2slot[i] = a;
-    }
-}
-
-__global__ void pair_capacity_check(long long S, const int *cf0, const unsigned *rev, int *bad)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride)
-        if ((long long)cf0[a] + (long long)cf0[rev[a]] > 0x7fffffffLL) atomicOr(bad, 4);
-}
-
-__global__ void narrow_caps(long long S, const long long *csum, int *cf0, int *cf, int *bad)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride) {
-        long long c = csum[a];
-        if (c > 0x7fffffffLL) {
-            atomicOr(bad, 2);
-            c = 0;
-        }
-        cf0[a] = (int)c;
-        cf[a] = (int)c;
+        if ((long long)cf0[a] + (long long)cf0[r] > 0x7fffffffLL) atomicOr(bad, 4);
     }
 }
 
@@ -408,11 +405,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             BUILD_CUDA(cudaStreamSynchronize(st));
         }
         g->slots = S;
-        u64 *ukey;
-        long long *csum;
         unsigned *slot_by_pos;
-        BUILD_ALLOC(ukey, u64, S, pool);
-        BUILD_ALLOC(csum, long long, S, pool);
         BUILD_ALLOC(slot_by_pos, unsigned, 2 * m, pool);
         OWN_ALLOC(g->col, int, S);
         OWN_ALLOC(g->cf, int, S);
@@ -420,16 +413,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         OWN_ALLOC(g->rev, unsigned, S);
         OWN_ALLOC(g->cfb, int, S);
         if (S > 0) {
-            BUILD_CUDA(cudaMemsetAsync(csum, 0, sizeof(long long) * S, st));
-            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cap, ukey, g->col, csum, slot_by_pos);
+            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, (int)n, k2s, v2s, heads, cap, (long long)S, g->col,
+                                                       g->cf0, g->cf, g->off, slot_by_pos, bad);
             BUILD_CUDA(cudaGetLastError());
-            narrow_caps<<<grid_for(S), 256, 0, st>>>(S, csum, g->cf0, g->cf, bad);
-            BUILD_CUDA(cudaGetLastError());
-            row_offsets<<<grid_for(S), 256, 0, st>>>(S, (int)n, ukey, kb, g->off);
-            BUILD_CUDA(cudaGetLastError());
-            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->rev, g->arc2slot);
-            BUILD_CUDA(cudaGetLastError());
-            pair_capacity_check<<<grid_for(S), 256, 0, st>>>(S, g->cf0, g->rev, bad);
+            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->cf0, g->rev, g->arc2slot, bad);
             BUILD_CUDA(cudaGetLastError());
         } else {
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
