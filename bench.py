@@ -62,13 +62,14 @@ def algorithmic_bytes(st: dict, n: int) -> int:
 
 def profiled_traffic():
     """DRAM bytes (read + write) of one solve launch from the committed ncu
-    summary, or None when solver.cu changed since that capture."""
+    summary, or None when the solver's device code (solver_impl.cuh) changed
+    since that capture."""
     import hashlib
     import re
     try:
         with open(os.path.join(ROOT, "profiles", "solve_kernel_rmat20.md")) as f:
             text = f.read()
-        with open(os.path.join(ROOT, "paper_2404_00270_gb300", "csrc", "solver.cu"), "rb") as f:
+        with open(os.path.join(ROOT, "paper_2404_00270_gb300", "csrc", "solver_impl.cuh"), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
         tag = re.search(r"sha256 prefix `([0-9a-f]+)`", text).group(1)
         if not sha.startswith(tag):
