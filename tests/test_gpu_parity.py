@@ -333,6 +333,15 @@ def test_bottom_up_bfs_same_results(layout, bu):
     check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o)
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_multi_source_rmat(layout):
+    """Eight far-apart source / sink pairs on R-MAT 13, joined by a super
+    source and a super sink (the multi-terminal construction of §4.1)."""
+    g = W.rmat_multi(13, 16, 5, 8)
+    src, dst, cap = g.numpy()
+    check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout)
+
+
 def test_autotune_keeps_the_value():
     from paper_2404_00270_gb300 import autotune
     m = wb()

@@ -195,6 +195,79 @@ def rmat(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19,
 
 
 # --------------------------------------------------------------------------
+# Multi-source / multi-sink instances (the construction of §4.1): k source /
+# sink pairs on one graph, joined by a super source S* = n (arcs S* -> s_i)
+# and a super sink T* = n + 1 (arcs t_i -> T*), appended after the graph's
+# arcs in pair order.  Each super arc carries the total capacity of the arcs
+# leaving s_i (resp. entering t_i), capped at 2^31 - 1, so it never limits
+# the flow.
+# --------------------------------------------------------------------------
+def multi_terminal(inst: FlowInstance, sources, sinks, name: str | None = None) -> FlowInstance:
+    sources = [int(x) for x in sources]
+    sinks = [int(x) for x in sinks]
+    if not sources or len(set(sources)) != len(sources) or len(set(sinks)) != len(sinks) or \
+            set(sources) & set(sinks):
+        raise ValueError("need distinct sources and sinks, disjoint from each other")
+    src, dst, cap = (x.cpu().long() for x in (inst.src, inst.dst, inst.cap))
+    n = inst.n
+    out_cap = torch.zeros(n, dtype=torch.int64).index_add_(0, src, cap)
+    in_cap = torch.zeros(n, dtype=torch.int64).index_add_(0, dst, cap)
+    S, T = n, n + 1
+    big = (1 << 31) - 1
+    s_idx = torch.tensor(sources, dtype=torch.int64)
+    t_idx = torch.tensor(sinks, dtype=torch.int64)
+    src2 = torch.cat([src, torch.full_like(s_idx, S), t_idx])
+    dst2 = torch.cat([dst, s_idx, torch.full_like(t_idx, T)])
+    cap2 = torch.cat([cap, out_cap[s_idx].clamp(max=big), in_cap[t_idx].clamp(max=big)])
+    dev = inst.src.device
+    return FlowInstance(name or f"{inst.name}-multi{len(sources)}", n + 2, src2.int().to(dev), dst2.int().to(dev),
+                        cap2.int().to(dev), S, T, dict(inst.meta, sources=sources, sinks=sinks))
+
+
+def far_pairs(inst: FlowInstance, k: int):
+    """k source / sink pairs far apart: the k largest out-degree vertices
+    (lowest id on ties) are the sources; each takes as sink the vertex
+    farthest from it by BFS over the arcs (lowest id on ties) among those it
+    reaches that are neither a source nor an earlier sink.  A source that
+    reaches no such vertex is skipped."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+    src, dst, _ = inst.numpy()
+    n = inst.n
+    outdeg = np.bincount(src, minlength=n)
+    order = np.lexsort((np.arange(n), -outdeg))
+    cand = [int(v) for v in order[: 4 * k] if outdeg[v] > 0]
+    A = sp.csr_matrix((np.ones(src.size), (src, dst)), shape=(n, n))
+    sources, sinks = [], []
+    for s0 in cand:
+        if len(sources) == k:
+            break
+        if s0 in sinks:
+            continue
+        d = shortest_path(A, unweighted=True, directed=True, indices=[s0])[0]
+        taken = set(cand[: 4 * k]) | set(sinks) | {s0}
+        best, far = -1, -1.0
+        for v in np.flatnonzero(np.isfinite(d)):
+            v = int(v)
+            if v in taken:
+                continue
+            if d[v] > far:
+                best, far = v, d[v]
+        if best >= 0:
+            sources.append(s0)
+            sinks.append(best)
+    return sources, sinks
+
+
+def rmat_multi(scale: int, edge_factor: int, seed: int, k: int, device="cpu") -> FlowInstance:
+    """R-MAT graph (as :func:`rmat`) with k far-apart source / sink pairs
+    joined by a super source and a super sink."""
+    base = rmat(scale, edge_factor, seed)
+    sources, sinks = far_pairs(base, k)
+    return multi_terminal(base, sources, sinks, f"rmat{scale}-multi{len(sources)}").to(device)
+
+
+# --------------------------------------------------------------------------
 # Bipartite matching as unit-capacity max-flow.  Left vertices 0..nl-1,
 # right vertices nl..nl+nr-1, s = nl+nr, t = nl+nr+1.  Left degrees follow a
 # discrete Zipf-Mandelbrot law p(d) ~ (d + delta)^(-exponent) on [1, dmax]
