@@ -94,7 +94,7 @@ typedef struct wbpr_options {
     int64_t batch_big_slots;  /* wbpr_maxflow_batch: instances with more residual
                                  slots than this are large (default 2^15); smaller
                                  ones are solved by a single block each */
-    int32_t bottom_up;        /* global-relabel BFS direction.  A level whose
+    int32_t bottom_up;        /* BFS direction (global relabel and min cut).  A level whose
                                  frontier F satisfies |F| * bottom_up >= (vertices
                                  not yet visited) and |F| >= bottom_up_min runs
                                  bottom-up: every unvisited vertex looks for a

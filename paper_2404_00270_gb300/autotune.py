@@ -2,12 +2,12 @@
 
 None of the knobs changes a result: the tile widths per degree class
 (`small_tile`, `small_max_degree`, `warp_max_degree`), the vertices each
-block covers (through `grid_blocks`) and the global-relabel frequency
-(`gr_ratio`).  The tuner times phase-1 solves of one graph under a grid of
-candidates, checks that every candidate finds the same flow value, and keeps
-the fastest.  Results are stored in a JSON table keyed by a coarse graph
-class (size, mean degree and hub skew), so later graphs of the same class
-start from the tuned options.
+block covers (through `grid_blocks`), the global-relabel frequency
+(`gr_ratio`) and the BFS direction rule (`bottom_up`).  The tuner times
+phase-1 solves of one graph under a grid of candidates, checks that every
+candidate finds the same flow value, and keeps the fastest.  Results are
+stored in a JSON table keyed by a coarse graph class (size, mean degree and
+hub skew), so later graphs of the same class start from the tuned options.
 """
 from __future__ import annotations
 
@@ -19,7 +19,7 @@ import os
 from . import (Options, WBPR_BCSR, wbpr_build, wbpr_default_options, wbpr_get_info,
                wbpr_get_stats, wbpr_maxflow, wbpr_set_options)
 
-KNOBS = ("small_tile", "small_max_degree", "warp_max_degree", "grid_blocks", "gr_ratio")
+KNOBS = ("small_tile", "small_max_degree", "warp_max_degree", "grid_blocks", "gr_ratio", "bottom_up")
 
 
 def graph_class(n: int, slots: int, max_degree: int) -> str:
@@ -35,9 +35,10 @@ def candidates(num_sms: int):
     warps = [256, 1024, 2048]
     grids = [0, num_sms, 2 * num_sms]
     ratios = [0.5, 1.0, 2.0]
-    for (tile, smax), wmax, grid, ratio in itertools.product(tiles, warps, grids, ratios):
+    directions = [14, 0]
+    for (tile, smax), wmax, grid, ratio, bu in itertools.product(tiles, warps, grids, ratios, directions):
         yield {"small_tile": tile, "small_max_degree": smax, "warp_max_degree": wmax,
-               "grid_blocks": grid, "gr_ratio": ratio}
+               "grid_blocks": grid, "gr_ratio": ratio, "bottom_up": bu}
 
 
 def _apply(opts: Options, cfg: dict) -> Options:

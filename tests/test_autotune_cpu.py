@@ -12,7 +12,7 @@ def test_graph_class_buckets():
 
 def test_candidates_cover_every_knob():
     c = list(A.candidates(152))
-    assert len(c) == 81
+    assert len(c) == 162
     for key in A.KNOBS:
         assert len({x[key] for x in c}) > 1
 
