@@ -1,20 +1,30 @@
 """Benchmark of the WBPR max-flow hot path on GB300.
 
-Workload (one GPU): R-MAT scale 20, edge factor 16 (a,b,c,d = .57,.19,.19,.05),
-self-loops and duplicates removed (16.09 M arcs), capacities U[1,1000],
-s = largest out-degree, t = largest in-degree; seeded, synthetic (stands in
-for the power-law SNAP graphs of the paper's Table 1).
+Headline workload (one GPU): R-MAT scale 26, edge factor 16 (a,b,c,d = .57,
+.19,.19,.05), self-loops and duplicates removed (1.06 G arcs), capacities
+U[1, 10^4], s = largest out-degree, t = largest in-degree, seed 4; seeded and
+synthetic (it stands in for the massive power-law SNAP graphs of the
+paper's Table 1).  BCSR with the reverse index, int64 excesses.
 
-One step = the whole hot path on that input, graph arrays resident in HBM:
-  build the BCSR residual graph (with reverse index) from device COO arrays,
-  maximum flow (preflow, push-relabel iterations with global relabel and gap,
-  phase 2 returning excess to s, per-arc flows), minimum cut (source side and
+One step = the whole hot path on that input, COO arrays resident in HBM:
+  build the BCSR residual graph from the device COO arrays, maximum flow
+  (preflow, push-relabel iterations with global relabel and gap, phase 2
+  returning excess to s, per-arc flows), minimum cut (source side and
   capacity), release.
 value = residual arcs scanned per second over the timed steps (entries read
 by the min-height scans of Alg. 2, both phases; see wbpr_stats).
 
---impl reference times the CPU oracle (FIFO push-relabel) on a bounded sample
-of the same workload (R-MAT scale 18, same parameters) on the host.
+Beside it, in `config`: the R-MAT 20 workload in both layouts (time to
+maximum flow, build, phase 1 + 2), the handle's HBM footprint against the
+O(V^2) adjacency matrix, the oracle's offline value for the R-MAT 26 graph,
+and a compact batch / serving block on the seeded mix of grids and
+bipartite graphs.  `cpu_baseline` times the oracle on the R-MAT 20 graph on
+one host core and reports both arms' time to solution on that same graph.
+
+--impl reference times the CPU oracle (FIFO push-relabel) per step on a
+bounded sample of the same workload family (R-MAT scale 18, same
+parameters) on the host.  --workload rmat20 makes R-MAT 20 the headline;
+--workload batch runs the batched / served mix alone.
 Under torchrun (N > 1) every rank solves its own replica (a single max-flow
 instance does not shard); value = the arcs all ranks scanned / the slowest
 rank's time.
@@ -22,6 +32,7 @@ rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -33,14 +44,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "residual arcs scanned/s (R-MAT 20 max-flow + min-cut, BCSR)"
 UNIT = "arcs/s"
+WORKLOADS = {
+    "rmat26": dict(scale=26, seed=4, cap_hi=10000),
+    "rmat20": dict(scale=20, seed=2, cap_hi=1000),
+}
 
 # The library's own kernels per step: the BCSR build (half_keys, tail_caps,
-# scatter_prefix, run_heads, merge_runs, pair_slots, max_degree_kernel),
-# solve_kernel for the flow and for the cut, and edge_flow_kernel.  CUB's
-# sort and scan kernels come on top.
-LAUNCHES_PER_STEP = 10
+# scatter_prefix, run_heads, merge_runs, pair_slots, max_degree_kernel; plus
+# count_degrees, iota_u32, invert_order, remap_arcs when the handle is
+# renumbered), solve_kernel for the flow and for the cut, and
+# edge_flow_kernel.  CUB's sort and scan kernels come on top.
+def launches_per_step(renumbered: bool) -> int:
+    return 10 + (4 if renumbered else 0)
+
 
 # Algorithmic bytes per unit of the BCSR solver (each unit is counted by the
 # kernel itself, see wbpr_get_stats).
@@ -51,32 +68,41 @@ B_PUSH = 52           # cf[k], cf[rev], cfb[k], cfb[rev] int32 RMW (32) + e(v) i
 B_RELABEL = 4
 B_GR_ENTRY = 12       # col 4 + cfb 4 (mirrored reverse residual) + h 4
 B_GR_VERTEX = 12      # per vertex per global relabel: h init/finalize, dead, queue
+B_RESET = 20          # per slot per solve: cf0 4 + cf 4 + cfb 4 read, cf 4 + cfb 4 written
 
 
-def algorithmic_bytes(st: dict, n: int) -> int:
+def algorithmic_bytes(st: dict, n: int, slots: int = 0) -> int:
+    """Bytes the method must move in one solve launch, from the kernel's own
+    counters; `slots` adds the reset of the residual graph."""
     return (B_ENTRY * st["arcs_scanned"] + B_ACTIVE * st["active_total"] +
             B_AVQ_SCAN * n * st["iterations"] + B_PUSH * st["pushes"] +
             B_RELABEL * st["relabels"] + B_GR_ENTRY * st["gr_arcs_scanned"] +
-            B_GR_VERTEX * n * st["global_relabels"])
+            B_GR_VERTEX * n * st["global_relabels"] + B_RESET * slots)
 
 
-def profiled_traffic():
-    """DRAM bytes (read + write) of one solve launch from the committed ncu
-    summary, or None when the solver's device code (solver_impl.cuh) changed
-    since that capture."""
-    import hashlib
-    import re
+def solver_sha() -> str:
+    with open(os.path.join(ROOT, "paper_2404_00270_gb300", "csrc", "solver_impl.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes (read + write) per solve launch from the machine-readable
+    ncu record profiles/solve_kernel_<workload>.json, or None when there is
+    none or the solver's device code changed since it was captured."""
     try:
-        with open(os.path.join(ROOT, "profiles", "solve_kernel_rmat20.md")) as f:
-            text = f.read()
-        with open(os.path.join(ROOT, "paper_2404_00270_gb300", "csrc", "solver_impl.cuh"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        tag = re.search(r"sha256 prefix `([0-9a-f]+)`", text).group(1)
-        if not sha.startswith(tag):
+        with open(os.path.join(ROOT, "profiles", f"solve_kernel_{workload}.json")) as f:
+            rec = json.load(f)
+        if not solver_sha().startswith(rec["solver_impl_sha256_prefix"]):
             return None
-        rd = int(re.search(r"dram__bytes_read\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
-        wr = int(re.search(r"dram__bytes_write\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
-        return rd + wr
+        return int(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def golden_rmat26():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_rmat26.json")) as f:
+            return json.load(f)
     except Exception:
         return None
 
@@ -169,26 +195,27 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_sample(seconds_budget: float = 20.0, scale: int = 18):
-    """The oracle, as it stands, on a bounded sample: R-MAT `scale`."""
+def metric_name(workload: str) -> str:
+    scale = WORKLOADS[workload]["scale"]
+    return f"residual arcs scanned/s (R-MAT {scale} max-flow + min-cut, BCSR)"
+
+
+def cpu_sample(scale: int = 20, seed: int = 2, cap_hi: int = 1000):
+    """The oracle, as it stands, on one host core: one solve (phase 1 +
+    phase 2 + edge flows + cut) of the R-MAT `scale` graph."""
     import oracle
     import workloads as W
     oracle.build()
-    g = W.rmat(scale, 16, 2)
+    g = W.rmat(scale, 16, seed, cap_lo=1, cap_hi=cap_hi)
     src, dst, cap = g.numpy()
-    runs, arcs, secs = 0, 0, 0.0
-    while secs < seconds_budget or runs == 0:
-        t0 = time.perf_counter()
-        r = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t, want_flow=True, want_cut=True)
-        secs += time.perf_counter() - t0
-        arcs += r["stats"]["arcs_scanned"]
-        runs += 1
-        if runs >= 3 and secs > seconds_budget / 2:
-            break
-    return {"value": arcs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"R-MAT scale {scale} (edge factor 16, seed 2, {g.m} arcs), FIFO push-relabel "
-                      f"phase 1 + 2 + cut, {runs} solves in {secs:.1f} s, 1 thread",
-            "time_to_solution_s": secs / runs}
+    t0 = time.perf_counter()
+    r = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t, want_flow=True, want_cut=True)
+    secs = time.perf_counter() - t0
+    return {"value": r["stats"]["arcs_scanned"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"R-MAT scale {scale} (edge factor 16, seed {seed}, {g.m} arcs; the R-MAT {scale} "
+                      f"workload itself), FIFO push-relabel phase 1 + 2 + edge flows + cut, one solve, "
+                      f"1 thread; unit = the oracle's own residual arcs examined",
+            "time_to_solution_s": secs, "flow_value": r["value"]}
 
 
 def run_reference(args):
@@ -210,20 +237,66 @@ def run_reference(args):
             arcs.append(r["stats"]["arcs_scanned"])
     total = sum(times)
     value = sum(arcs) / total
-    sample = f"R-MAT scale 18 (edge factor 16, seed 2, {g.m} arcs) per step, oracle phase 1 + 2 + cut"
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+    sample = (f"R-MAT scale 18 (edge factor 16, seed 2, {g.m} arcs) per step, a bounded sample of the "
+              f"R-MAT workload family; oracle phase 1 + 2 + edge flows + cut, 1 thread")
+    workload = args.workload if args.workload in WORKLOADS else "rmat26"
+    line = {"metric": metric_name(workload), "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "rmat18-sample-of-rmat20", "layout": "adjacency list (oracle)"},
+            "config": {"workload": f"rmat18-sample-of-{workload}", "layout": "adjacency list (oracle)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
+def layout_block(wb, g, stream, layouts, reps: int = 3) -> dict:
+    """Per layout, with the graph resident: time to maximum flow (phase 1,
+    value only; median of `reps` solves), phase 1 + 2 with edge flows, build
+    time, and time to solution (build + maximum flow with edge flows + cut,
+    device inputs, host-timed)."""
+    import torch
+    n, m, s, t = g.n, g.m, g.s, g.t
+    flow = torch.empty(max(1, m), dtype=torch.int32, device=g.src.device)
+    side = torch.empty(n, dtype=torch.uint8, device=g.src.device)
+    out = {}
+    for name, layout in layouts:
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, layout, None, stream)
+        torch.cuda.synchronize()
+        build_ms = 1e3 * (time.perf_counter() - tb)
+        vals, t_ms, arcs_l = [], [], []
+        for _ in range(reps):
+            vals.append(wb.wbpr_maxflow(G, stream))
+            st = wb.wbpr_get_stats(G)
+            t_ms.append(st["solve_ms"])
+            arcs_l.append(st["arcs_scanned"])
+        wb.wbpr_maxflow(G, stream, flow)
+        st2 = wb.wbpr_get_stats(G)
+        info = wb.wbpr_get_info(G)
+        G.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, layout, None, stream)
+        v = wb.wbpr_maxflow(G, stream, flow)
+        c = wb.wbpr_mincut(G, stream, side)
+        G.close()
+        torch.cuda.synchronize()
+        tts_ms = 1e3 * (time.perf_counter() - t0)
+        assert len(set(vals)) == 1 and vals[0] == v == c
+        out[name] = {"value": vals[0], "time_to_maxflow_ms": statistics.median(t_ms),
+                     "arcs_per_s": statistics.median(arcs_l) / (statistics.median(t_ms) / 1e3),
+                     "build_ms": build_ms, "phase1_plus_phase2_ms": st2["solve_ms"],
+                     "time_to_solution_ms": tts_ms,
+                     "iterations": st2["iterations"], "global_relabels": st2["global_relabels"],
+                     "device_bytes": info["device_bytes"], "slots": info["slots"],
+                     "grid_blocks": info["grid_blocks"], "renumbered": bool(info["renumbered"])}
+    return out
+
+
 def run_gpu(args):
-    import numpy as np
     import torch
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -237,7 +310,8 @@ def run_gpu(args):
     wb.use_torch_allocator(True)
     stream = torch.cuda.current_stream()
 
-    g = W.rmat(args.scale, 16, 2, device=dev)
+    wl = WORKLOADS[args.workload]
+    g = W.rmat(wl["scale"], 16, wl["seed"], cap_lo=1, cap_hi=wl["cap_hi"], device=dev)
     n, m, s, t = g.n, g.m, g.s, g.t
     flow = torch.empty(m, dtype=torch.int32, device=dev)
     side = torch.empty(n, dtype=torch.uint8, device=dev)
@@ -247,19 +321,20 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def step(layout):
-        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, layout, None, stream)
+    def step():
+        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, wb.WBPR_BCSR, None, stream)
         v = wb.wbpr_maxflow(G, stream, flow)
         st = wb.wbpr_get_stats(G)
         c = wb.wbpr_mincut(G, stream, side)
+        info = wb.wbpr_get_info(G)
         G.close()
-        return v, c, st
+        return v, c, st, info
 
-    # warm-up
-    for _ in range(args.warmup):
-        v0, c0, _ = step(wb.WBPR_BCSR)
+    for _ in range(max(1, args.warmup)):
+        v0, c0, _, info0 = step()
     assert v0 == c0
 
+    torch.cuda.reset_peak_memory_stats(dev)
     sampler = ClockSampler(local)
     sampler.start()
     barrier()
@@ -271,114 +346,128 @@ def run_gpu(args):
     alg_bytes = 0
     value_seen = None
     for _ in range(args.steps):
-        v, c, st = step(wb.WBPR_BCSR)
+        v, c, st, info = step()
         arcs += st["arcs_scanned"]
         solve_ms += st["solve_ms"]
-        alg_bytes += algorithmic_bytes(st, n)
+        alg_bytes += algorithmic_bytes(st, n, info["slots"])
         value_seen = v
+        assert v == c == v0
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
+    peak_bytes = torch.cuda.max_memory_allocated(dev)
     ms = ev0.elapsed_time(ev1)
     ms, arcs_all = aggregate_ranks(ms, float(arcs), dev)
     value = arcs_all / (ms / 1e3)
 
-    # time-to-maxflow with the graph resident (phase 1, value only), both layouts
-    breakdown = {}
-    for name, layout in (() if args.quick else (("bcsr", wb.WBPR_BCSR), ("rcsr", wb.WBPR_RCSR))):
-        torch.cuda.synchronize()
-        tb = time.perf_counter()
-        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, layout, None, stream)
-        torch.cuda.synchronize()
-        build_ms = 1e3 * (time.perf_counter() - tb)
-        reps = 3
-        vals, t_ms, arcs_l = [], [], []
-        for _ in range(reps):
-            vals.append(wb.wbpr_maxflow(G, stream))
-            st = wb.wbpr_get_stats(G)
-            t_ms.append(st["solve_ms"])
-            arcs_l.append(st["arcs_scanned"])
-        wb.wbpr_maxflow(G, stream, flow)
-        st2 = wb.wbpr_get_stats(G)
-        info = wb.wbpr_get_info(G)
-        G.close()
-        breakdown[name] = {"value": vals[0], "time_to_maxflow_ms": statistics.median(t_ms),
-                           "arcs_per_s": statistics.median(arcs_l) / (statistics.median(t_ms) / 1e3),
-                           "build_ms": build_ms, "phase1_plus_phase2_ms": st2["solve_ms"],
-                           "iterations": st2["iterations"], "global_relabels": st2["global_relabels"],
-                           "device_bytes": info["device_bytes"], "grid_blocks": info["grid_blocks"]}
-        assert len(set(vals)) == 1 and vals[0] == value_seen
+    # the headline graph resident (BCSR), and R-MAT 20 in both layouts
+    headline = {} if args.quick else layout_block(wb, g, stream, [("bcsr", wb.WBPR_BCSR)])
+    c2 = {}
+    if not args.quick:
+        if args.workload == "rmat20":
+            c2 = layout_block(wb, g, stream, [("bcsr", wb.WBPR_BCSR), ("rcsr", wb.WBPR_RCSR)])
+        else:
+            g20 = W.rmat(20, 16, 2, device=dev)
+            c2 = layout_block(wb, g20, stream, [("bcsr", wb.WBPR_BCSR), ("rcsr", wb.WBPR_RCSR)])
+            c2["workload"] = f"rmat20 (n {g20.n}, m {g20.m}, seed 2, capacities U[1,1000])"
+            del g20
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    hsrc = g.src.cpu().pin_memory()
-    hdst = g.dst.cpu().pin_memory()
-    hcap = g.cap.cpu().pin_memory()
-    hflow = torch.empty(m, dtype=torch.int32).pin_memory()
-    hside = torch.empty(n, dtype=torch.uint8).pin_memory()
-    e_steps = 0 if args.quick else max(1, min(args.steps, 5))
-    barrier()
-    t0 = time.perf_counter()
-    e_arcs = 0
-    for _ in range(e_steps):
-        G = wb.wbpr_build(n, m, hsrc, hdst, hcap, s, t, wb.WBPR_BCSR, None, stream)
-        v = wb.wbpr_maxflow(G, stream, hflow)
-        e_arcs += wb.wbpr_get_stats(G)["arcs_scanned"]
-        c = wb.wbpr_mincut(G, stream, hside)
-        G.close()
-    barrier()
-    e_ms = 1e3 * (time.perf_counter() - t0)
-    e2e = {"value": e_arcs / (e_ms / 1e3) * (world if world > 1 else 1) if e_steps else None,
-           "unit": UNIT, "h2d_bytes_per_step": 12 * m, "d2h_bytes_per_step": 4 * m + n + 16,
-           "ms_per_step": e_ms / e_steps if e_steps else None}
+    e_steps = 0 if args.quick else max(1, min(args.steps, 3))
+    e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 12 * m, "d2h_bytes_per_step": 4 * m + n + 16}
+    if e_steps:
+        hsrc = g.src.cpu().pin_memory()
+        hdst = g.dst.cpu().pin_memory()
+        hcap = g.cap.cpu().pin_memory()
+        hflow = torch.empty(m, dtype=torch.int32).pin_memory()
+        hside = torch.empty(n, dtype=torch.uint8).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        e_arcs = 0
+        for _ in range(e_steps):
+            G = wb.wbpr_build(n, m, hsrc, hdst, hcap, s, t, wb.WBPR_BCSR, None, stream)
+            ve = wb.wbpr_maxflow(G, stream, hflow)
+            e_arcs += wb.wbpr_get_stats(G)["arcs_scanned"]
+            ce = wb.wbpr_mincut(G, stream, hside)
+            G.close()
+            assert ve == ce == value_seen
+        barrier()
+        e_ms = 1e3 * (time.perf_counter() - t0)
+        e_ms, e_arcs_all = aggregate_ranks(e_ms, float(e_arcs), dev)
+        e2e["value"] = e_arcs_all / (e_ms / 1e3)
+        e2e["ms_per_step"] = e_ms / e_steps
+        del hsrc, hdst, hcap, hflow, hside
 
     peak, peak_kind = measured_peaks()
     launch_ms = solve_ms / args.steps
     achieved = (alg_bytes / args.steps) / (launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic() if args.scale == 20 else None
+    traffic = profiled_traffic(args.workload)
+    footprint = {"handle_bytes": info0["device_bytes"], "peak_device_bytes_in_step": peak_bytes,
+                 "coo_bytes": 12 * m, "adjacency_matrix_bytes_2B_per_cell": 2 * n * n,
+                 "matrix_over_handle": 2 * n * n / info0["device_bytes"]}
+    config = {"workload": f"{args.workload}-maxflow-mincut", "scale": wl["scale"], "edge_factor": 16,
+              "seed": wl["seed"], "capacities": f"U[1,{wl['cap_hi']}]", "n": n, "m": m, "s": s, "t": t,
+              "layout": "bcsr+rev", "renumbered": bool(info0["renumbered"]),
+              "parallelism": "replicas" if world > 1 else "single",
+              "l2": f"inputs larger than L2 (COO {12 * m / 1e6:.0f} MB, BCSR handle "
+                    f"{info0['device_bytes'] / 1e6:.0f} MB per step); no flush needed",
+              "flow_value": value_seen,
+              "time_to_maxflow_ms": headline["bcsr"]["time_to_maxflow_ms"] if headline else None,
+              "resident": headline, "footprint": footprint, "layouts_rmat20": c2}
+    gold = golden_rmat26() if args.workload == "rmat26" else None
+    if gold:
+        config["oracle_offline"] = {"value": gold["value"], "equal": gold["value"] == value_seen,
+                                    "wall_s": gold["oracle_wall_s"], "host": gold["host"],
+                                    "source": "tests/golden/oracle_rmat26.json"}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"rmat{args.scale}-maxflow-mincut", "scale": args.scale, "edge_factor": 16,
-                   "n": n, "m": m, "s": s, "t": t, "layout": "bcsr+rev",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": (f"inputs larger than L2 (COO {12 * m / 1e6:.0f} MB"
-                          + (f", BCSR handle {breakdown['bcsr']['device_bytes'] / 1e6:.0f} MB" if breakdown else "")
-                          + " per step)"),
-                   "flow_value": value_seen,
-                   "time_to_maxflow_ms": breakdown["bcsr"]["time_to_maxflow_ms"] if breakdown else None,
-                   "layouts": breakdown},
+        "metric": metric_name(args.workload), "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": config,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel",
+                     "launch_ms": launch_ms, "algorithmic_bytes_per_launch": alg_bytes / args.steps,
                      "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"},
-        "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+        "gpu_launches": args.steps * launches_per_step(bool(info0["renumbered"])),
         "clocks": clocks,
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_sample(args.cpu_seconds)
+        cb = cpu_sample(20, 2, 1000)
+        if c2:
+            gpu_tts = c2["bcsr"]["time_to_solution_ms"] / 1e3
+            cb["gpu_time_to_solution_s"] = gpu_tts
+            cb["speedup_time_to_solution"] = cb["time_to_solution_s"] / gpu_tts
+            assert cb["flow_value"] == c2["bcsr"]["value"]
+        line["cpu_baseline"] = cb
+    if rank == 0 and world == 1 and not args.quick and args.batch_block > 0:
+        line["config"]["batch"] = batch_measure(args.batch_block, steps=3, warmup=1, plain_sample=24,
+                                                serve_count=args.batch_block, serve_rates=[1.0])
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
 
-
-def run_batch(args):
-    """The batched / served workload: a seeded mix of grids and bipartite
-    graphs of uneven size, solved (a) one instance per launch, (b) all in one
-    batched launch, (c) through the continuous-batching server with Poisson
-    arrivals."""
+def batch_measure(count: int, steps: int, warmup: int, plain_sample: int, serve_count: int,
+                  serve_rates, check_oracle: bool = False) -> dict:
+    """The batched / served workload: `count` instances of the seeded mix of
+    grids and bipartite graphs of uneven size, solved (a) one instance per
+    launch on an evenly spaced sample, (b) all in one batched launch per step,
+    (c) through the continuous-batching server with Poisson arrivals at
+    fractions of the batched rate.  Every batched and served value must equal
+    the one-at-a-time value of the same instance (and the oracle's with
+    `check_oracle`)."""
     import numpy as np
     import torch
     import paper_2404_00270_gb300 as wb
     from paper_2404_00270_gb300 import serve
     import workloads as W
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     wb.load()
     wb.use_torch_allocator(True)
     stream = torch.cuda.current_stream()
-    specs = W.batch_spec(args.batch_count)
+    specs = W.batch_spec(count)
     t0 = time.perf_counter()
     insts = [W.make_from_spec(sp, device=dev) for sp in specs]
     torch.cuda.synchronize()
@@ -389,8 +478,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     # (a) one instance per launch, on an evenly spaced sample
-    step = max(1, len(graphs) // args.plain_sample)
-    sample = list(range(0, len(graphs), step))
+    stride = max(1, len(graphs) // plain_sample)
+    sample = list(range(0, len(graphs), stride))
     plain_ms, plain_vals = [], {}
     for i in sample:
         torch.cuda.synchronize()
@@ -398,27 +487,34 @@ def run_batch(args):
         plain_vals[i] = wb.wbpr_maxflow(graphs[i], stream)
         plain_ms.append(1e3 * (time.perf_counter() - ta))
     plain_rate = len(sample) / (sum(plain_ms) / 1e3)
+    oracle_checked = 0
+    if check_oracle:
+        import oracle
+        for i in sample:
+            src, dst, cap = insts[i].numpy()
+            ref = oracle.maxflow_pr(insts[i].n, src, dst, cap, insts[i].s, insts[i].t, False, False)["value"]
+            assert ref == plain_vals[i], (i, ref, plain_vals[i])
+            oracle_checked += 1
     # (b) the whole mix in one batched launch per step
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         vals = wb.wbpr_maxflow_batch(graphs, stream)
     assert all(vals[i] == plain_vals[i] for i in sample)
-    sampler = ClockSampler(0)
-    sampler.start()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         vals = wb.wbpr_maxflow_batch(graphs, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
+    assert all(vals[i] == plain_vals[i] for i in sample)
     batch_rate = len(graphs) / (ms / 1e3)
     inst_ms = [wb.wbpr_get_stats(G)["solve_ms"] for G in graphs]
     slowest = sorted(range(len(graphs)), key=lambda i: -inst_ms[i])[:5]
     slowest = [{"spec": list(specs[i]), "ms": inst_ms[i], "team_blocks": wb.wbpr_get_info(graphs[i])["grid_blocks"]}
                for i in slowest]
+    batch_vals = list(vals)
     for G in graphs:
         G.close()
     del graphs
@@ -426,8 +522,8 @@ def run_batch(args):
     # (c) continuous batching with Poisson arrivals at a fraction of the batch rate
     serving = {}
     rng = np.random.default_rng(5)
-    n_serve = min(len(insts), args.serve_count)
-    for frac in args.serve_rates:
+    n_serve = min(len(insts), serve_count)
+    for frac in serve_rates:
         lam = frac * batch_rate
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_serve))
         reqs = [serve.Request(i, g.n, g.src, g.dst, g.cap, g.s, g.t, float(a))
@@ -435,25 +531,35 @@ def run_batch(args):
         free_b, _ = torch.cuda.mem_get_info()
         srv = serve.Server(int(0.5 * free_b))
         out = srv.run(reqs)
-        bad = [r.rid for r in out if r.rid in plain_vals and r.value != plain_vals[r.rid]]
+        bad = [r.rid for r in out if r.value != batch_vals[r.rid]]
         assert not bad, bad
         summ = serve.latency_summary(out)
         summ["rate_per_s"] = lam
         serving[f"{frac:g}x"] = summ
+    return {"instances": len(insts), "arcs": total_arcs, "generate_s": gen_s, "build_s": build_s,
+            "layout": "bcsr+rev", "batched_solves_per_s": batch_rate, "batch_ms": ms,
+            "plain_solves_per_s": plain_rate, "plain_sample": len(sample),
+            "plain_p50_ms": float(np.percentile(plain_ms, 50)),
+            "plain_p99_ms": float(np.percentile(plain_ms, 99)),
+            "speedup_vs_plain": batch_rate / plain_rate, "oracle_checked": oracle_checked,
+            "slowest_in_batch": slowest, "serving": serving}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = batch_measure(args.batch_count, args.steps, args.warmup, args.plain_sample, args.serve_count,
+                        args.serve_rates)
+    clocks = sampler.stop()
     line = {
-        "metric": f"batched solves/s ({len(insts):,}-instance mix, one batched launch)", "value": batch_rate,
-        "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"batch-mix-{len(insts)}", "instances": len(insts), "arcs": total_arcs,
-                   "generate_s": gen_s, "build_s": build_s, "layout": "bcsr+rev",
-                   "plain_solves_per_s": plain_rate, "plain_sample": len(sample),
-                   "plain_p50_ms": float(np.percentile(plain_ms, 50)),
-                   "plain_p99_ms": float(np.percentile(plain_ms, 99)),
-                   "speedup_vs_plain": batch_rate / plain_rate,
-                   "batch_ms": ms, "slowest_in_batch": slowest, "serving": serving},
-        "roofline": None, "clocks": clocks,
-        "gpu_launches": args.steps * 2,
+        "metric": f"batched solves/s ({res['instances']:,}-instance mix, one batched launch)",
+        "value": res["batched_solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["batch_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(res, workload=f"batch-mix-{res['instances']}"),
+        "roofline": None, "clocks": clocks, "gpu_launches": args.steps * 2,
     }
     print(json.dumps(line))
 
@@ -465,20 +571,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wbpr", choices=["wbpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the benchmark workload)")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch"])
+    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "rmat20", "batch"])
+    ap.add_argument("--batch-block", type=int, default=256,
+                    help="instances of the batch / serving block in config (0 = none)")
     ap.add_argument("--batch-count", type=int, default=1024)
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=512)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0])
     args = ap.parse_args()
-    if args.workload == "batch" and args.impl != "reference":
-        run_batch(args)
-        return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -60,7 +60,11 @@ typedef enum {
 /* Tuning knobs.  None of them changes a result; all of them change speed. */
 typedef struct wbpr_options {
     int32_t use_rev;          /* BCSR backward-slot lookup: 1 = reverse index (default),
-                                 0 = binary search in the neighbour's row (§3.2) */
+                                 0 = binary search in the neighbour's row (§3.2).
+                                 Taken at build time: a handle built with 0 holds
+                                 neither the reverse index nor the mirrored reverse
+                                 residual (8 bytes per slot less) and refuses a
+                                 later switch to 1 (WBPR_ESTATE) */
     int32_t gap;              /* 1 = gap heuristic on (default), 0 = off */
     int32_t multi_push;       /* 1 = discharge pass: the owner of u pushes along every
                                  arc read as lower in one pass, then relabels if excess
@@ -102,6 +106,12 @@ typedef struct wbpr_options {
                                  Otherwise top-down.  0 = always top-down.
                                  Default 14 */
     int32_t bottom_up_min;    /* default 1024 */
+    int32_t renumber;         /* vertex numbering of the solver, fixed at build time:
+                                 1 = renumber by endpoint count, largest first
+                                 (the heights that residual scans gather from
+                                 share cache sectors), 0 = input ids, -1 = automatic
+                                 (default: on from 2^22 vertices).  Results are in
+                                 input ids either way. */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */
@@ -130,6 +140,8 @@ typedef struct wbpr_info {
     int64_t device_bytes;      /* device memory held by the handle */
     int32_t grid_blocks;       /* persistent grid used by the solver */
     int32_t num_sms;
+    int32_t renumbered;        /* 1 when the solver numbers vertices differently
+                                  from the input (wbpr_options.renumber) */
 } wbpr_info;
 
 /*
@@ -243,7 +255,11 @@ wbpr_status wbpr_set_allocator(wbpr_alloc_fn alloc, wbpr_free_fn free_fn, void *
  *     WBPR_STAGE_ITERATIONS       `arg` push-relabel iterations of Alg. 2 on
  *                                 the current state, without global relabel
  *   wbpr_export(g, what, host_dst, count): copy `count` elements of an
- *     internal array to host memory (synchronous).
+ *     internal array to host memory (synchronous).  Per-vertex arrays and the
+ *     layout are in the solver's vertex numbering: the input ids, unless the
+ *     handle was renumbered (wbpr_options.renumber), in which case
+ *     WBPR_ARRAY_ORDER maps each solver id to its input id and WBPR_ARRAY_ST
+ *     gives the solver ids of s and t.
  */
 enum {
     WBPR_STAGE_PREFLOW = 1,
@@ -268,7 +284,10 @@ enum {
     WBPR_ARRAY_TRACE = 14,       /* uint64[4 * records]: per grid barrier of the last
                                     launch: barrier id, queue generation, globaltimer ns,
                                     queue sizes (24 bits per tile class) */
-    WBPR_ARRAY_TRACE_LEN = 15    /* uint32[1]: records in the trace */
+    WBPR_ARRAY_TRACE_LEN = 15,   /* uint32[1]: records in the trace */
+    WBPR_ARRAY_ORDER = 16,       /* int32[n]: input id of each solver vertex id
+                                    (0 elements when the handle is not renumbered) */
+    WBPR_ARRAY_ST = 17           /* int32[2]: solver ids of s and t (host copy) */
 };
 wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg);
 wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64_t count);
@@ -297,7 +316,12 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
  *   d_residual NULL, or device int32[slots]: receives the residual capacity
  *              of every slot at the end of the solve (cap - residual is the
  *              flow of a maximum preflow).
- * Synchronises `stream` and returns the solve's status.  The first call on a
+ * Before solving, a kernel checks the arrays: off[0] = 0, off[n] = slots, rows
+ * non-decreasing, neighbour ids in [0, n), capacities >= 0, and rev[] pairing
+ * every slot with one in its neighbour's row that points back.  Arrays that
+ * fail return WBPR_EINVAL and nothing is solved.  The call synchronises
+ * `stream` (twice: after the check and after the solve) and returns the
+ * solve's status.  The first call on a
  * device looks up the array's device address (once per device, with that
  * device current); make that first call before any stream capture.  Every
  * call shares the one array, which keeps the last call's contents (the call
@@ -355,6 +379,11 @@ wbpr_server *wbpr_server_start(const wbpr_server_options *opts);
 int64_t wbpr_server_submit(wbpr_server *srv, wbpr_graph *g);  /* ticket >= 0, or a negative wbpr_status */
 wbpr_status wbpr_server_poll(wbpr_server *srv, int64_t ticket, int64_t *value);
 wbpr_status wbpr_server_stop(wbpr_server *srv);
+/* Device interval of a finished request: the server kernel's globaltimer (ns)
+ * when its team started and finished the solve.  WBPR_OK once the request is
+ * done (as wbpr_server_poll reports), 1 while it is pending.  The values stay
+ * readable until wbpr_server_stop. */
+wbpr_status wbpr_server_times(wbpr_server *srv, int64_t ticket, uint64_t *t_start_ns, uint64_t *t_end_ns);
 /* Diagnostics once the server kernel has ended (1 while it still runs): for
  * each of the first `count` teams (large teams first, then single blocks) why
  * it left: 0 still running, 1 end of its ring, 2 stop flag, 3 idle limit,

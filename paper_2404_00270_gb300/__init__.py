@@ -35,7 +35,8 @@ ARRAY = {"height": (1, np.int32), "excess": (2, np.int64), "offsets": (3, np.int
          "col": (4, np.int32), "cf": (5, np.int32), "cap": (6, np.int32), "rev": (7, np.uint32),
          "bf": (8, np.int32), "in_offsets": (9, np.int64), "in_col": (10, np.int32),
          "flow_idx": (11, np.uint32), "arc2slot": (12, np.uint32), "excess_total": (13, np.int64),
-         "trace": (14, np.uint64), "trace_len": (15, np.uint32)}
+         "trace": (14, np.uint64), "trace_len": (15, np.uint32), "order": (16, np.int32),
+         "st": (17, np.int32)}
 
 # Every function declared in include/wbpr.h.
 EXPORTED_SYMBOLS = [
@@ -45,7 +46,7 @@ EXPORTED_SYMBOLS = [
     "wbpr_last_error", "wbpr_last_error_message", "wbpr_error_string", "wbpr_set_allocator",
     "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc",
     "wbpr_server_default_options", "wbpr_server_start", "wbpr_server_submit", "wbpr_server_poll",
-    "wbpr_server_stop", "wbpr_server_team_exits",
+    "wbpr_server_stop", "wbpr_server_team_exits", "wbpr_server_times",
 ]
 
 
@@ -63,7 +64,8 @@ class Options(ctypes.Structure):
                 ("barrier_timeout_ms", ctypes.c_int32), ("max_iterations", ctypes.c_int64),
                 ("trace", ctypes.c_int32), ("gr_ratio", ctypes.c_float),
                 ("batch_team", ctypes.c_int32), ("batch_big_slots", ctypes.c_int64),
-                ("bottom_up", ctypes.c_int32), ("bottom_up_min", ctypes.c_int32)]
+                ("bottom_up", ctypes.c_int32), ("bottom_up_min", ctypes.c_int32),
+                ("renumber", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,7 +86,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("s", ctypes.c_int32),
                 ("t", ctypes.c_int32), ("layout", ctypes.c_int32), ("slots", ctypes.c_int64),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("grid_blocks", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("num_sms", ctypes.c_int32),
+                ("renumbered", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -150,11 +153,12 @@ def load(build_if_missing: bool = False):
         lib.wbpr_server_poll.argtypes = [_P, i64, _P]
         lib.wbpr_server_stop.argtypes = [_P]
         lib.wbpr_server_team_exits.argtypes = [_P, _P, i32]
+        lib.wbpr_server_times.argtypes = [_P, i64, _P, _P]
         for name in ("wbpr_maxflow", "wbpr_maxflow_async", "wbpr_solve_status", "wbpr_mincut",
                      "wbpr_maxflow_batch", "wbpr_get_options", "wbpr_set_options",
                      "wbpr_get_stats", "wbpr_get_info", "wbpr_last_error", "wbpr_set_allocator",
                      "wbpr_run_stage", "wbpr_export", "wbpr_maxflow_bcsr_noalloc", "wbpr_server_poll",
-                     "wbpr_server_stop", "wbpr_server_team_exits"):
+                     "wbpr_server_stop", "wbpr_server_team_exits", "wbpr_server_times"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
         return lib
@@ -352,8 +356,8 @@ def wbpr_export(g: Graph, what: str, count: int | None = None) -> np.ndarray:
     if count is None:
         info = wbpr_get_info(g)
         count = {"height": info["n"], "excess": info["n"], "offsets": info["n"] + 1,
-                 "in_offsets": info["n"] + 1, "arc2slot": info["m"], "excess_total": 1}.get(
-                     what, info["slots"])
+                 "in_offsets": info["n"] + 1, "arc2slot": info["m"], "excess_total": 1,
+                 "order": info["n"] if info["renumbered"] else 0, "st": 2}.get(what, info["slots"])
     if what == "trace":
         length = wbpr_export(g, "trace_len", 1)[0] if wbpr_get_options(g).trace > 0 else 0
         out = np.zeros(4 * int(length), dtype=dt)
@@ -416,6 +420,17 @@ def wbpr_server_poll(server: int, ticket: int):
         return None
     _check(rc)
     return v.value
+
+
+def wbpr_server_times(server: int, ticket: int):
+    """(start, end) of a finished request on the device's globaltimer in ns,
+    else None while it is pending."""
+    a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = load().wbpr_server_times(server, int(ticket), ctypes.byref(a), ctypes.byref(b))
+    if rc == 1:
+        return None
+    _check(rc)
+    return a.value, b.value
 
 
 def wbpr_server_stop(server: int) -> None:

@@ -100,6 +100,7 @@ void wbpr_default_options(wbpr_options *o)
     o->batch_big_slots = (int64_t)1 << 15;
     o->bottom_up = 14;
     o->bottom_up_min = 1024;
+    o->renumber = -1;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -144,6 +145,7 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->batch_team < 1 || o->batch_team > 64 || (o->batch_team & (o->batch_team - 1))) return WBPR_EINVAL;
     if (o->batch_big_slots < 0) return WBPR_EINVAL;
     if (o->bottom_up < 0 || o->bottom_up > (1 << 20) || o->bottom_up_min < 1) return WBPR_EINVAL;
+    if (o->renumber < -1 || o->renumber > 1) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -237,6 +239,7 @@ wbpr_graph *wbpr_build_ex(int64_t n, int64_t m, const int32_t *src, const int32_
     g->t = t;
     g->layout = layout;
     g->opts = o;
+    g->renumbered = o.renumber == 1 || (o.renumber == -1 && n >= kRenumberAutoVertices);
     memset(&g->stats, 0, sizeof(g->stats));
     auto fail = [&](wbpr_status code, const std::string &msg) -> wbpr_graph * {
         wbpr_status keep = t_last == WBPR_OK ? code : t_last;
@@ -317,6 +320,10 @@ wbpr_status wbpr_set_options(wbpr_graph *g, const wbpr_options *o)
 {
     if (!g || !o) return set_error(WBPR_EINVAL, "wbpr_set_options: NULL argument");
     if (check_options(o) != WBPR_OK) return set_error(WBPR_EINVAL, "wbpr_set_options: invalid options");
+    if (o->renumber != g->opts.renumber)
+        return set_error(WBPR_ESTATE, "wbpr_set_options: renumber is fixed when the handle is built");
+    if (g->layout == WBPR_BCSR && o->use_rev && !g->rev)
+        return set_error(WBPR_ESTATE, "wbpr_set_options: the handle was built without the reverse index (use_rev = 0)");
     g->opts = *o;
     return WBPR_OK;
 }
@@ -342,6 +349,7 @@ wbpr_status wbpr_get_info(const wbpr_graph *g, wbpr_info *info)
     info->device_bytes = g->device_bytes;
     info->grid_blocks = g->grid_blocks;
     info->num_sms = g->num_sms;
+    info->renumbered = g->order != nullptr;
     return WBPR_OK;
 }
 
@@ -384,8 +392,9 @@ Params make_params(wbpr_graph *g, int mode)
     Params p;
     memset(&p, 0, sizeof(p));
     p.g.n = (int)g->n;
-    p.g.s = g->s;
-    p.g.t = g->t;
+    p.g.s = g->s_int;
+    p.g.t = g->t_int;
+    p.g.order = g->order;
     p.g.slots = g->slots;
     p.g.off = g->off;
     p.g.col = g->col;
@@ -521,7 +530,7 @@ wbpr_status wbpr_maxflow(wbpr_graph *g, wbpr_stream_t stream, int64_t *value, in
     if (rc != WBPR_OK) return rc;
     rc = collect(g, st, false);
     if (rc != WBPR_OK) return rc;
-    API_CUDA(cudaMemcpyAsync(g->pinned, g->e + g->t, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaMemcpyAsync(g->pinned, g->e + g->t_int, sizeof(long long), cudaMemcpyDeviceToHost, st));
     if (want_flow) {
         const bool dev = is_device_ptr(edge_flow);
         int *out = edge_flow;
@@ -552,7 +561,7 @@ wbpr_status wbpr_maxflow_async(wbpr_graph *g, wbpr_stream_t stream, int64_t *d_v
     int mode = kModePreflow | kModePhase1 | (want_flow ? kModePhase2 : 0);
     wbpr_status rc = launch_solver(g, st, mode, 0, nullptr);
     if (rc != WBPR_OK) return rc;
-    API_CUDA(cudaMemcpyAsync(d_value, g->e + g->t, sizeof(long long), cudaMemcpyDeviceToDevice, st));
+    API_CUDA(cudaMemcpyAsync(d_value, g->e + g->t_int, sizeof(long long), cudaMemcpyDeviceToDevice, st));
     if (want_flow)
         API_CUDA(launch_edge_flow(g->layout, g->m, g->arc2slot, g->cf0, g->cf, g->bf, g->prefix,
                                   g->cap_in, d_edge_flow, st));
@@ -667,6 +676,15 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
     case WBPR_ARRAY_ARC2SLOT: src = g->arc2slot; avail = g->m; break;
     case WBPR_ARRAY_EXCESS_TOTAL: src = &g->ctl->excess_total; elem = 8; avail = 1; break;
     case WBPR_ARRAY_TRACE_LEN: src = &g->ctl->trace_len; elem = 4; avail = 1; break;
+    case WBPR_ARRAY_ORDER: src = g->order; avail = g->order ? g->n : 0; break;
+    case WBPR_ARRAY_ST: {
+        static_assert(sizeof(int32_t) == 4, "");
+        int32_t *out = (int32_t *)host_dst;
+        if (count > 2) return set_error(WBPR_EINVAL, "wbpr_export: count exceeds the array");
+        if (count > 0) out[0] = g->s_int;
+        if (count > 1) out[1] = g->t_int;
+        return WBPR_OK;
+    }
     case WBPR_ARRAY_TRACE: {
         unsigned len = 0;
         if (g->trace) API_CUDA(cudaMemcpy(&len, &g->ctl->trace_len, sizeof(len), cudaMemcpyDeviceToHost));

@@ -115,10 +115,14 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
 // from one side) writes the slot's column, sums the capacities of the run's
 // tail-side half-entries into cf0 / cf (flag 2 on int32 overflow), and writes
 // the offsets of the rows that start at its slot (rows with no slot take the
-// next row's start).  Runs are short: one per (u, v), as long as the number
-// of duplicate arcs between u and v.
+// next row's start).  The run's head-side half-entries are the arcs col ->
+// row, so their capacities sum to the paired slot's cf0: the pair's total
+// must fit int32 (flag 4), since a push moves residual capacity from one slot
+// to the other, and with the mirror (cfb != null) it is the initial cfb.
+// Runs are short: one per (u, v), as long as the number of duplicate arcs
+// between u and v.
 __global__ void merge_runs(long long len, int b, int n, const u64 *key, const unsigned *pos, const unsigned *slot_of,
-                           const int *cap, long long S, int *col, int *cf0, int *cf, long long *off,
+                           const int *cap, long long S, int *col, int *cf0, int *cf, int *cfb, long long *off,
                            unsigned *slot_by_pos, int *bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -130,17 +134,23 @@ __global__ void merge_runs(long long len, int b, int n, const u64 *key, const un
         const u64 kp = j == 0 ? ~0ull : key[j - 1];
         if (k == kp) continue;
         col[a] = (int)(k & mask);
-        long long sum = 0;
+        long long sum = 0, back = 0;
         for (long long i = j; i < len && key[i] == k; ++i) {
             const unsigned p = pos[i];
             if ((p & 1u) == 0) sum += cap[p >> 1];
+            else back += cap[p >> 1];
         }
         if (sum > 0x7fffffffLL) {
             atomicOr(bad, 2);
             sum = 0;
         }
+        if (sum + back > 0x7fffffffLL) {
+            atomicOr(bad, 4);
+            back = 0;
+        }
         cf0[a] = (int)sum;
         cf[a] = (int)sum;
+        if (cfb) cfb[a] = (int)back;
         const long long r = (long long)(k >> b);
         const long long rp = j == 0 ? -1 : (long long)(kp >> b);
         for (long long v = rp + 1; v <= r; ++v) off[v] = a;
@@ -150,20 +160,21 @@ __global__ void merge_runs(long long len, int b, int n, const u64 *key, const un
 }
 
 // The two half-entries of input arc i sit in mutually reverse slots;
-// arc2slot of the arc is the slot of its tail-side half-entry.  The pair's
-// capacities must fit int32 together (flag 4), since a push moves residual
-// capacity from one slot to the other.
+// arc2slot of the arc is the slot of its tail-side half-entry.  rev is null
+// when the handle keeps no reverse index (backward lookup by binary search).
 __global__ void pair_slots(long long m, const int *src, const int *dst, const unsigned *slot_by_pos,
-                           const int *cf0, unsigned *rev, unsigned *arc2slot, int *bad)
+                           unsigned *rev, unsigned *arc2slot)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
         if (src[i] == dst[i]) continue;  // self-loop: no slot
-        const unsigned a = slot_by_pos[2 * i], r = slot_by_pos[2 * i + 1];
-        rev[a] = r;
-        rev[r] = a;
+        const unsigned a = slot_by_pos[2 * i];
+        if (rev) {
+            const unsigned r = slot_by_pos[2 * i + 1];
+            rev[a] = r;
+            rev[r] = a;
+        }
         arc2slot[i] = a;
-        if ((long long)cf0[a] + (long long)cf0[r] > 0x7fffffffLL) atomicOr(bad, 4);
     }
 }
 
@@ -177,6 +188,47 @@ __global__ void row_offsets(long long S, int n, const u64 *key, int shift, long 
         for (long long v = rp + 1; v <= r; ++v) off[v] = a;
         if (a == S - 1)
             for (long long v = r + 1; v <= n; ++v) off[v] = S;
+    }
+}
+
+// Renumbering (wbpr_options.renumber): endpoint counts per vertex, then the
+// input arcs' endpoints mapped to the new ids.  Ids are checked here, since
+// the remap indexes by them (flag 1: out of range or negative capacity).
+__global__ void count_degrees(long long m, int n, const int *src, const int *dst, const int *cap,
+                              unsigned *deg, int *bad)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int u = src[i], v = dst[i];
+        if (u < 0 || u >= n || v < 0 || v >= n || cap[i] < 0) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        if (u == v) continue;
+        atomicAdd(deg + u, 1u);
+        atomicAdd(deg + v, 1u);
+    }
+}
+
+__global__ void iota_u32(long long len, unsigned *p)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += stride) p[i] = (unsigned)i;
+}
+
+// order[j] = the input id of new vertex j; perm is its inverse.
+__global__ void invert_order(long long n, const int *order, int *perm)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += stride) perm[order[j]] = (int)j;
+}
+
+__global__ void remap_arcs(long long m, const int *perm, const int *src, const int *dst, int *rsrc, int *rdst)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
+        rsrc[i] = perm[src[i]];
+        rdst[i] = perm[dst[i]];
     }
 }
 
@@ -321,6 +373,57 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
     int h_bad = 0;
     unsigned long long h_nonloop = 0;
 
+    // ---- optional renumbering by endpoint count, largest first ---------------
+    // Vertices that many arcs point to get neighbouring ids, so the heights the
+    // residual scans gather (h[col]) share sectors and stay in L2.  The solver
+    // runs on the new ids; the cut side is written back in input ids, edge
+    // flows are per input arc, and s, t are mapped here.
+    g->s_int = g->s;
+    g->t_int = g->t;
+    g->order = nullptr;
+    if (g->renumbered && m > 0) {
+        unsigned *deg, *degs, *ids;
+        BUILD_ALLOC(deg, unsigned, n, pool);
+        BUILD_ALLOC(degs, unsigned, n, pool);
+        BUILD_ALLOC(ids, unsigned, n, pool);
+        OWN_ALLOC(g->order, int, n);
+        BUILD_CUDA(cudaMemsetAsync(deg, 0, sizeof(unsigned) * (size_t)n, st));
+        count_degrees<<<grid_for(m), 256, 0, st>>>(m, (int)n, src, dst, cap, deg, bad);
+        iota_u32<<<grid_for(n), 256, 0, st>>>(n, ids);
+        BUILD_CUDA(cudaGetLastError());
+        BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaStreamSynchronize(st));
+        if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
+        size_t nb = 0;
+        // stable: equal counts keep increasing input ids
+        BUILD_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, nb, deg, degs, ids, (unsigned *)g->order,
+                                                             (int64_t)n, 0, 32, st));
+        void *t0 = pool.get(nb);
+        if (!t0) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+        BUILD_CUDA(cub::DeviceRadixSort::SortPairsDescending(t0, nb, deg, degs, ids, (unsigned *)g->order,
+                                                             (int64_t)n, 0, 32, st));
+        pool.release(t0);
+        pool.release(ids);
+        pool.release(degs);
+        pool.release(deg);
+        int *perm, *rsrc, *rdst;
+        BUILD_ALLOC(perm, int, n, pool);
+        BUILD_ALLOC(rsrc, int, m, pool);
+        BUILD_ALLOC(rdst, int, m, pool);
+        invert_order<<<grid_for(n), 256, 0, st>>>(n, g->order, perm);
+        remap_arcs<<<grid_for(m), 256, 0, st>>>(m, perm, src, dst, rsrc, rdst);
+        BUILD_CUDA(cudaGetLastError());
+        int st_int[2];
+        BUILD_CUDA(cudaMemcpyAsync(&st_int[0], perm + g->s, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaMemcpyAsync(&st_int[1], perm + g->t, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BUILD_CUDA(cudaStreamSynchronize(st));
+        pool.release(perm);
+        g->s_int = st_int[0];
+        g->t_int = st_int[1];
+        src = rsrc;
+        dst = rdst;
+    }
+
     OWN_ALLOC(g->arc2slot, unsigned, m);
     OWN_ALLOC(g->off, long long, n + 1);
     unsigned long long *h_maxdeg_dev = counter + 1;
@@ -410,13 +513,17 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         OWN_ALLOC(g->col, int, S);
         OWN_ALLOC(g->cf, int, S);
         OWN_ALLOC(g->cf0, int, S);
-        OWN_ALLOC(g->rev, unsigned, S);
-        OWN_ALLOC(g->cfb, int, S);
+        // The reverse index and the mirrored reverse residual only when the
+        // handle uses them (paper mode, use_rev = 0, saves 8 bytes per slot).
+        if (g->opts.use_rev) {
+            OWN_ALLOC(g->rev, unsigned, S);
+            OWN_ALLOC(g->cfb, int, S);
+        }
         if (S > 0) {
             merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, (int)n, k2s, v2s, heads, cap, (long long)S, g->col,
-                                                       g->cf0, g->cf, g->off, slot_by_pos, bad);
+                                                       g->cf0, g->cf, g->cfb, g->off, slot_by_pos, bad);
             BUILD_CUDA(cudaGetLastError());
-            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->cf0, g->rev, g->arc2slot, bad);
+            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->rev, g->arc2slot);
             BUILD_CUDA(cudaGetLastError());
         } else {
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);

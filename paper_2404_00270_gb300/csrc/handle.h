@@ -30,7 +30,9 @@ wbpr_status set_error(wbpr_status st, const std::string &msg);
 
 struct wbpr_graph {
     int64_t n = 0, m = 0;
-    int32_t s = 0, t = 0;
+    int32_t s = 0, t = 0;     // as given (input ids)
+    int32_t s_int = 0, t_int = 0;  // the solver's ids (differ when renumbered)
+    bool renumbered = false;  // vertices renumbered by the builder (order != null)
     int32_t layout = 0;
     int64_t slots = 0;        // BCSR merged entries / RCSR arcs without loops
     int64_t mprime = 0;       // input arcs that are not self-loops
@@ -44,6 +46,7 @@ struct wbpr_graph {
     bool solved_value = false;
 
     // graph (device)
+    int *order = nullptr;     // renumbered: solver id -> input id
     long long *off = nullptr;
     int *col = nullptr;
     int *cf = nullptr;

@@ -74,6 +74,40 @@ wbpr_status scratch_address(int device, unsigned char **out)
     return WBPR_OK;
 }
 
+// Checks the caller's BCSR arrays before a solve trusts them: off[0] = 0,
+// off[n] = slots, rows non-decreasing, neighbours in [0, n), capacities >= 0,
+// and rev[] a pairing of slots whose partner lies in the neighbour's row and
+// points back to the owner.  Any failure stores WBPR_EINVAL in *err.  Reads
+// only off[0..n] and the [slots] arrays; the row of a slot is found by binary
+// search over off.
+__global__ void noalloc_check_kernel(int n, long long slots, const long long *off, const int *col,
+                                     const int *cap, const unsigned *rev, int *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0 && (off[0] != 0 || off[n] != slots)) atomicCAS(err, 0, (int)WBPR_EINVAL);
+    for (long long v = tid; v < n; v += stride)
+        if (off[v] > off[v + 1]) atomicCAS(err, 0, (int)WBPR_EINVAL);
+    if (off[0] != 0 || off[n] != slots) return;
+    for (long long k = tid; k < slots; k += stride) {
+        const int w = col[k];
+        const unsigned r = rev[k];
+        if (w < 0 || w >= n || cap[k] < 0 || (long long)r >= slots) {
+            atomicCAS(err, 0, (int)WBPR_EINVAL);
+            continue;
+        }
+        // owner row of k: the last v with off[v] <= k
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (int)(((long long)lo + hi + 1) >> 1);
+            if (off[mid] <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        if (rev[r] != (unsigned)k || col[r] != lo || (long long)r < off[w] || (long long)r >= off[w + 1])
+            atomicCAS(err, 0, (int)WBPR_EINVAL);
+    }
+}
+
 }  // namespace
 }  // namespace wbpr
 
@@ -144,7 +178,10 @@ extern "C" wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32
     wbpr_options o;
     wbpr_default_options(&o);
     p.mode = kModePreflow | kModePhase1;
-    p.cycle = 16;
+    p.g.layout_tag = kBCSR;
+    p.mirror_gather = 1;                     // the scratch may hold another graph's residuals
+    p.gr_ratio = o.gr_ratio;                 // the time-balanced trigger of wbpr_maxflow,
+    p.cycle = o.gr_ratio > 0.f ? 1000 : 16;  // with its automatic cycle cap
     p.gap = o.gap;
     p.use_rev = 1;
     p.multi_push = o.multi_push;
@@ -156,12 +193,29 @@ extern "C" wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32
     p.timeout_ns = (unsigned long long)o.barrier_timeout_ms * 1000000ull;
 
     // The control block must start at zero; everything else is reset by the kernel.
+    // The caller's arrays are checked first (the error word of the control block).
+    int err = 0;
     cudaError_t e = cudaMemsetAsync(p.st.ctl, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) {
+        long long cb = (slots > n ? slots : n) / 256 + 1;
+        if (cb > 4LL * num_sms) cb = 4LL * num_sms;
+        noalloc_check_kernel<<<(int)cb, 256, 0, st>>>(n, slots, (const long long *)off, col, cap, rev,
+                                                      &p.st.ctl->err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &p.st.ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WBPR_ECUDA, std::string("wbpr_maxflow_bcsr_noalloc: ") + cudaGetErrorString(e));
+    }
+    if (err != 0)
+        return set_error(WBPR_EINVAL, "wbpr_maxflow_bcsr_noalloc: malformed BCSR arrays (offsets, neighbour ids, "
+                                      "capacities or reverse slots)");
     if (e == cudaSuccess) e = solver_launch(kBCSR, 8, (int)grid, p, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_value, p.st.e + t, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && d_residual && slots > 0)
         e = cudaMemcpyAsync(d_residual, p.g.cf, sizeof(int32_t) * (size_t)slots, cudaMemcpyDeviceToDevice, st);
-    int err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &p.st.ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {

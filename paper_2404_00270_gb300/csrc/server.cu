@@ -270,7 +270,13 @@ wbpr_status wbpr_server_poll(wbpr_server *s, int64_t ticket, int64_t *value)
     if (!s || ticket < 0) return set_error(WBPR_EINVAL, "wbpr_server_poll: bad arguments");
     const int cls = (int)(ticket >> 40);
     const unsigned i = (unsigned)(ticket & ((1ll << 40) - 1));
-    if (cls > 1 || i >= s->published[cls]) return set_error(WBPR_EINVAL, "wbpr_server_poll: unknown ticket");
+    wbpr_graph *g = nullptr;
+    {
+        // A submit on another host thread may grow graphs[cls] meanwhile.
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (cls > 1 || i >= s->published[cls]) return set_error(WBPR_EINVAL, "wbpr_server_poll: unknown ticket");
+        g = s->graphs[cls][i];
+    }
     volatile ServerOut *o = s->h_out[cls] + i;
     if (o->done == 0) {
         // still pending -- unless the kernel is gone (stopped, idle timeout, error)
@@ -282,7 +288,6 @@ wbpr_status wbpr_server_poll(wbpr_server *s, int64_t ticket, int64_t *value)
                                               cudaGetErrorString(q) + "; a team gives up after idle_ms without requests)");
     }
     std::atomic_thread_fence(std::memory_order_acquire);
-    wbpr_graph *g = s->graphs[cls][i];
     memset(&g->stats, 0, sizeof(g->stats));
     g->stats.iterations = o->iterations;
     g->stats.solve_ms = (double)(o->t_end - o->t_start) * 1e-6;
@@ -290,6 +295,23 @@ wbpr_status wbpr_server_poll(wbpr_server *s, int64_t ticket, int64_t *value)
     if (value) *value = o->value;
     g->solved_value = true;
     g->solved_flow = false;
+    return WBPR_OK;
+}
+
+wbpr_status wbpr_server_times(wbpr_server *s, int64_t ticket, uint64_t *t_start_ns, uint64_t *t_end_ns)
+{
+    if (!s || ticket < 0 || !t_start_ns || !t_end_ns) return set_error(WBPR_EINVAL, "wbpr_server_times: bad arguments");
+    const int cls = (int)(ticket >> 40);
+    const unsigned i = (unsigned)(ticket & ((1ll << 40) - 1));
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (cls > 1 || i >= s->published[cls]) return set_error(WBPR_EINVAL, "wbpr_server_times: unknown ticket");
+    }
+    volatile ServerOut *o = s->h_out[cls] + i;
+    if (o->done == 0) return (wbpr_status)1;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    *t_start_ns = o->t_start;
+    *t_end_ns = o->t_end;
     return WBPR_OK;
 }
 

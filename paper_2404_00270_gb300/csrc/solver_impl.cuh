@@ -1173,13 +1173,19 @@ constexpr int kBuThread = 32;
 constexpr int kBuStep = 4;
 
 // Over entry k of v's list (neighbour w returned): the residual capacity of
-// v -> w (backward BFS) or of w -> v (forward BFS).
+// v -> w (backward BFS) or of w -> v (forward BFS; BCSR without the mirror:
+// the reverse slot by index or by binary search in w's row).
 template <int L, int DIR>
-__device__ __forceinline__ int bu_res(const GraphDev &g, long long k, bool in, int &w)
+__device__ __forceinline__ int bu_res(const Params &P, int v, long long k, bool in, int &w)
 {
+    const GraphDev &g = P.g;
     if (L == kBCSR) {
         w = __ldg(g.col + k);
-        return DIR == kBfsBackward ? __ldcg(g.cf + k) : __ldcg(g.cfb + k);
+        if (DIR == kBfsBackward) return __ldcg(g.cf + k);
+        if (g.cfb) return __ldcg(g.cfb + k);
+        const long long ra = P.use_rev ? (long long)__ldg(g.rev + k)
+                                       : lower_bound_col(g.col, __ldg(g.off + w), __ldg(g.off + w + 1), v);
+        return __ldcg(g.cf + ra);
     }
     if (!in) {  // out slot of v: arc v -> w; its reverse residual is its flow
         w = __ldg(g.col + k);
@@ -1215,7 +1221,7 @@ __device__ __forceinline__ void bu_found(Ctx &c, int v, long long deg, int val, 
 // Scan W-lane groups of NB entries of v's row starting at row index r0 + sl;
 // true if one of them is a residual arc into the frontier.
 template <int L, int DIR, int W, int NB>
-__device__ __forceinline__ bool bu_scan(const Params &P, long long ob, long long dout, long long ib,
+__device__ __forceinline__ bool bu_scan(const Params &P, int v, long long ob, long long dout, long long ib,
                                         long long deg, long long r0, int sl, int want)
 {
     int w[NB], r[NB];
@@ -1227,7 +1233,7 @@ __device__ __forceinline__ bool bu_scan(const Params &P, long long ob, long long
         if (rr < deg) {
             bool in;
             const long long k = row_slot<L>(ob, dout, ib, rr, in);
-            r[q] = bu_res<L, DIR>(P.g, k, in, w[q]);
+            r[q] = bu_res<L, DIR>(P, v, k, in, w[q]);
         }
     }
     const int *lvl = bfs_levels<DIR>(P);
@@ -1292,7 +1298,7 @@ __device__ void bfs_level_bu(Ctx &c, int val)
 #pragma unroll
             for (int i = 0; i < kBuVerts; ++i) {
                 hit[i] = false;
-                if (live[i]) hit[i] = bu_scan<L, DIR, 1, kBuStep>(P, ob[i], dout[i], ib[i], deg[i], r0, 0, want);
+                if (live[i]) hit[i] = bu_scan<L, DIR, 1, kBuStep>(P, v[i], ob[i], dout[i], ib[i], deg[i], r0, 0, want);
             }
 #pragma unroll
             for (int i = 0; i < kBuVerts; ++i) {
@@ -1315,7 +1321,7 @@ __device__ void bfs_level_bu(Ctx &c, int val)
                 d += __ldg(g.in_off + u + 1) - ii;
             }
             for (long long r0 = 0; r0 < d; r0 += 32 * kBuStep) {
-                const bool h1 = bu_scan<L, DIR, 32, kBuStep>(P, o, dO, ii, d, r0, lane, want);
+                const bool h1 = bu_scan<L, DIR, 32, kBuStep>(P, u, o, dO, ii, d, r0, lane, want);
                 if (lane == 0) scanned += d - r0 < 32 * kBuStep ? d - r0 : 32 * kBuStep;
                 if (__any_sync(kFull, h1)) {
                     if (lane == 0) bu_found<L, DIR>(c, u, d, val, nset, n3);
@@ -1333,7 +1339,7 @@ __device__ void bfs_level_bu(Ctx &c, int val)
                 d += __ldg(g.in_off + u + 1) - ii;
             }
             for (long long r0 = 0; r0 < d; r0 += (long long)kBlock * kBuStep) {
-                const bool h1 = bu_scan<L, DIR, kBlock, kBuStep>(P, o, dO, ii, d, r0, threadIdx.x, want);
+                const bool h1 = bu_scan<L, DIR, kBlock, kBuStep>(P, u, o, dO, ii, d, r0, threadIdx.x, want);
                 if (threadIdx.x == 0) scanned += d - r0 < kBlock * kBuStep ? d - r0 : kBlock * kBuStep;
                 if (__syncthreads_or(h1)) {
                     if (threadIdx.x == 0) bu_found<L, DIR>(c, u, d, val, nset, n3);
@@ -1631,6 +1637,11 @@ __device__ bool run_phase(Ctx &c, bool phase1, long long *it_total)
 }
 
 // Reset the residual graph and state, then the preflow of Alg. 1 step 0.
+// The mirror cfb[a] = cf[rev[a]] is reset to cf0[rev[a]] without a gather: a
+// push moves capacity between the two slots of a pair, so cf[a] + cf[rev[a]]
+// (= cf[a] + cfb[a]) stays cf0[a] + cf0[rev[a]] in every state the solver
+// leaves behind (the builder starts from cf = cf0, cfb = cf0[rev]).  Only a
+// caller whose arrays may hold another graph's state asks for the gather.
 template <int L>
 __device__ bool preflow(Ctx &c)
 {
@@ -1639,9 +1650,13 @@ __device__ bool preflow(Ctx &c)
     const long long stride = (long long)c.nblk * kBlock;
     const long long tid = c.bid * kBlock + threadIdx.x;
     for (long long k = tid; k < g.slots; k += stride) {
-        g.cf[k] = __ldg(g.cf0 + k);
+        const int c0 = __ldg(g.cf0 + k);
+        if (L == kBCSR && g.cfb) {
+            if (P.mirror_gather) g.cfb[k] = __ldg(g.cf0 + __ldg(g.rev + k));
+            else g.cfb[k] = __ldcg(g.cf + k) + __ldcg(g.cfb + k) - c0;
+        }
+        g.cf[k] = c0;
         if (L == kRCSR) g.bf[k] = 0;
-        if (L == kBCSR && g.cfb) g.cfb[k] = __ldg(g.cf0 + __ldg(g.rev + k));
     }
     for (long long v = tid; v < g.n; v += stride) {
         P.st.e[v] = 0;
@@ -1692,8 +1707,9 @@ __device__ bool min_cut(Ctx &c)
     seed_queue<L>(c, c.gen, g.s);
     if (!grid_sync(c, 30)) return false;
     // Forward BFS from s, bottom-up on large frontiers (the forward residual
-    // w -> v of an entry of v's row needs cfb in BCSR).
-    const bool bu_ok = P.bottom_up > 0 && (L == kRCSR || g.cfb != nullptr);
+    // w -> v of an entry of v's row: the mirror cfb in BCSR, else a lookup of
+    // the reverse slot).
+    const bool bu_ok = P.bottom_up > 0;
     long long seen = 0;
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
@@ -1711,7 +1727,8 @@ __device__ bool min_cut(Ctx &c)
     long long bs = block_sum(c, sum);
     if (threadIdx.x == 0 && bs) atomicAdd((u64 *)&P.st.ctl->cut_value, (u64)bs);
     if (P.source_side)
-        for (long long v = tid; v < n; v += stride) P.source_side[v] = (unsigned char)(__ldcg(mark + v) != 0);
+        for (long long v = tid; v < n; v += stride)
+            P.source_side[g.order ? __ldg(g.order + v) : v] = (unsigned char)(__ldcg(mark + v) != 0);
     return grid_sync(c, 32);
 }
 

@@ -27,6 +27,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kClasses = 3;         // tile classes: small tile, warp, block
 constexpr int kQueueCap = 1024;     // per-class shared-memory staging of queue appends
 constexpr int kUnvisited = 0x7fffffff;
+constexpr long long kRenumberAutoVertices = 1LL << 22;  // renumber = -1: on from this many vertices
 constexpr int kChunk = 2048;        // hub rows are processed in chunks of this many entries,
                                     // one chunk per block, taken dynamically
 
@@ -82,6 +83,7 @@ struct GraphDev {
     const long long *in_off;    // RCSR
     const int *in_col;          // RCSR
     const unsigned *flow_idx;   // RCSR
+    const int *order;           // renumbered handle: solver id -> input id (cut side output); or null
 };
 
 // Upper bound on the hub chunks of one queue generation: every hub has at
@@ -140,6 +142,8 @@ struct Params {
     unsigned char *source_side;  // kModeCut output (device, n bytes) or null
     unsigned long long *trace;   // optional: 4 words per grid barrier (where, gen, ns, queue total)
     int trace_cap;               // records
+    int mirror_gather;           // reset cfb[a] = cf0[rev[a]] by gather (cf and cfb may hold another
+                                 // graph's state) instead of from the pair invariant
 };
 
 // Persistent server (solver.cu).  The rings, results, published counts and

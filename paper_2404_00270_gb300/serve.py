@@ -22,7 +22,7 @@ import torch
 from . import (WBPR_BCSR, load, torch_allocator_enabled, use_torch_allocator, wbpr_build,
                wbpr_get_info, wbpr_server_default_options,
                wbpr_server_poll, wbpr_server_start, wbpr_server_stop, wbpr_server_submit,
-               wbpr_server_team_exits)
+               wbpr_server_team_exits, wbpr_server_times)
 
 
 @dataclasses.dataclass
@@ -40,6 +40,7 @@ class Request:
     done: float | None = None
     footprint: int = 0
     build_ms: float = 0.0
+    device_ns: tuple | None = None  # (start, end) of the solve on the device's globaltimer
 
     @property
     def m(self) -> int:
@@ -139,6 +140,7 @@ class Server:
                     if v is not None:
                         req.value = v
                         req.done = time.perf_counter() - t0
+                        req.device_ns = wbpr_server_times(srv, ticket)
                         done.append(ticket)
                 if done or not outstanding:
                     last_progress = time.perf_counter()
@@ -157,6 +159,20 @@ class Server:
         return requests
 
 
+def max_overlap(requests) -> int:
+    """Most requests whose device solves were in progress at one instant."""
+    ev = []
+    for r in requests:
+        if getattr(r, "device_ns", None):
+            ev.append((r.device_ns[0], 1))
+            ev.append((r.device_ns[1], -1))
+    best = cur = 0
+    for _, d in sorted(ev, key=lambda x: (x[0], x[1])):
+        cur += d
+        best = max(best, cur)
+    return best
+
+
 def latency_summary(requests) -> dict:
     lat = sorted(r.done - r.arrival for r in requests)
     n = len(lat)
@@ -166,4 +182,5 @@ def latency_summary(requests) -> dict:
     last = max(r.done for r in requests)
     q = lambda p: lat[min(n - 1, int(p * (n - 1) + 0.5))]
     return {"solves": n, "solves_per_s": n / max(1e-9, last - first), "p50_ms": 1e3 * q(0.50),
-            "p99_ms": 1e3 * q(0.99), "max_ms": 1e3 * lat[-1], "makespan_s": last - first}
+            "p99_ms": 1e3 * q(0.99), "max_ms": 1e3 * lat[-1], "makespan_s": last - first,
+            "max_concurrent_on_device": max_overlap(requests)}

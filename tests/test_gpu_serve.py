@@ -59,3 +59,6 @@ def test_served_results_equal_alone():
     assert srv.peak_in_use <= budget + max(r.footprint for r in out)
     summ = serve.latency_summary(out)
     assert summ["solves"] == len(insts) and summ["p99_ms"] >= summ["p50_ms"] > 0
+    # the solves overlapped on the device: some were in progress at the same time
+    assert all(r.device_ns and r.device_ns[1] >= r.device_ns[0] for r in out)
+    assert summ["max_concurrent_on_device"] >= 2

@@ -1,5 +1,5 @@
 """Host logic of the serving loop that needs no GPU."""
-from paper_2404_00270_gb300.serve import footprint_estimate, latency_summary
+from paper_2404_00270_gb300.serve import footprint_estimate, latency_summary, max_overlap
 
 
 class _R:
@@ -19,3 +19,12 @@ def test_latency_summary_percentiles():
 
 def test_footprint_grows_with_size():
     assert footprint_estimate(10, 10) < footprint_estimate(10, 20) < footprint_estimate(20, 20)
+
+
+def test_max_overlap_of_device_intervals():
+    class _D:
+        def __init__(self, a, b):
+            self.device_ns = (a, b)
+    assert max_overlap([_D(0, 10), _D(10, 20), _D(20, 30)]) == 1   # touching ends do not overlap
+    assert max_overlap([_D(0, 10), _D(5, 15), _D(6, 7), _D(14, 30)]) == 3
+    assert max_overlap([]) == 0
