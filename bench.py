@@ -564,6 +564,78 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def warp_distribution(w) -> dict:
+    """Per-warp busy times normalised by their mean (the distribution of
+    §4.3, Fig. 3): spread and quantiles."""
+    import numpy as np
+    w = np.asarray(w, np.float64)
+    if w.size == 0 or w.mean() <= 0:
+        return {}
+    x = w / w.mean()
+    return {"warps": int(w.size), "mean_us": float(w.mean() / 1e3), "std_over_mean": float(x.std()),
+            "max_over_mean": float(x.max()),
+            "quantiles_over_mean": {f"p{q}": float(np.percentile(x, q)) for q in (5, 25, 50, 75, 95)}}
+
+
+def run_ablation(args):
+    """Vertex-centric (VC, the method) against thread-centric (TC, the
+    lock-free baseline of Alg. 1): the comparison of the paper's Tables 1-2
+    and Fig. 3 on the R-MAT 20 and bipartite 2^20 workloads, both layouts,
+    with the discharge pass and with the paper's one-push rule.  Per
+    configuration: time to maximum flow (phase 1, median of up to 3 solves;
+    one when a solve takes over 2 s), iterations, and the per-warp busy-time
+    distribution."""
+    import torch
+    import paper_2404_00270_gb300 as wb
+    import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wb.load()
+    wb.use_torch_allocator(True)
+    stream = torch.cuda.current_stream()
+    graphs = {"rmat20": lambda: W.rmat(20, 16, 2, device=dev),
+              "bipartite20": lambda: W.bipartite_zipf(1 << 20, 1 << 20, 3, device=dev)}
+    rows = []
+    for gname, make in graphs.items():
+        g = make()
+        for lname, layout in (("bcsr", wb.WBPR_BCSR), ("rcsr", wb.WBPR_RCSR)):
+            for mp in (1, 0):
+                for tc in (0, 1):
+                    o = wb.wbpr_default_options()
+                    o.thread_centric, o.multi_push, o.warp_time = tc, mp, 1
+                    G = wb.wbpr_build(g.n, g.m, g.src, g.dst, g.cap, g.s, g.t, layout, o, stream)
+                    times, vals = [], []
+                    for _ in range(3):
+                        vals.append(wb.wbpr_maxflow(G, stream))
+                        st = wb.wbpr_get_stats(G)
+                        times.append(st["solve_ms"])
+                        if st["solve_ms"] > 2000:
+                            break
+                    w = wb.wbpr_export(G, "warp_time")
+                    G.close()
+                    assert len(set(vals)) == 1
+                    rows.append({"graph": gname, "layout": lname, "approach": "TC" if tc else "VC",
+                                 "push_rule": "discharge pass" if mp else "one push (Alg. 1)",
+                                 "value": vals[0], "time_to_maxflow_ms": statistics.median(times),
+                                 "iterations": st["iterations"], "arcs_scanned": st["arcs_scanned"],
+                                 "warps": warp_distribution(w)})
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del g
+        torch.cuda.empty_cache()
+    speedups = {}
+    for r in rows:
+        if r["approach"] == "VC":
+            tcr = next(x for x in rows if x["approach"] == "TC" and all(
+                x[k] == r[k] for k in ("graph", "layout", "push_rule")))
+            assert tcr["value"] == r["value"]
+            speedups[f"{r['graph']}/{r['layout']}/{r['push_rule']}"] = tcr["time_to_maxflow_ms"] / r["time_to_maxflow_ms"]
+    line = {"metric": "time to maximum flow, thread-centric / vertex-centric (speedup of VC)",
+            "value": statistics.mean(speedups.values()), "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "ablation-vc-tc", "speedups": speedups, "rows": rows}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,7 +644,7 @@ def main():
     ap.add_argument("--impl", default="wbpr", choices=["wbpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
-    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "rmat20", "batch"])
+    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "rmat20", "batch", "ablation"])
     ap.add_argument("--batch-block", type=int, default=256,
                     help="instances of the batch / serving block in config (0 = none)")
     ap.add_argument("--batch-count", type=int, default=1024)
@@ -584,6 +656,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     else:
         run_gpu(args)
 

@@ -112,6 +112,21 @@ typedef struct wbpr_options {
                                  share cache sectors), 0 = input ids, -1 = automatic
                                  (default: on from 2^22 vertices).  Results are in
                                  input ids either way. */
+    int32_t thread_centric;   /* 1 = the thread-centric baseline of §2.2 / §4 (TC):
+                                 every thread owns fixed vertices, checks them for
+                                 activity itself and scans an active vertex's whole
+                                 residual list alone; no active-vertex queue, no
+                                 degree classes.  0 = vertex-centric (default). */
+    int32_t warp_time;        /* 1 = record, per warp of the grid, the device time
+                                 spent in push-relabel passes (taken by the warp's
+                                 first lane, summed over the solve); read with
+                                 wbpr_export(WBPR_ARRAY_WARP_TIME).  Default 0. */
+    int32_t barrier_extra;    /* for tests of the device wait limit only: every grid
+                                 barrier waits for this many arrivals more than the
+                                 grid has, so its wait runs out after
+                                 barrier_timeout_ms and the solve returns
+                                 WBPR_ETIMEOUT (0..1024, default 0; grids of one
+                                 block do not wait) */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */
@@ -287,7 +302,10 @@ enum {
     WBPR_ARRAY_TRACE_LEN = 15,   /* uint32[1]: records in the trace */
     WBPR_ARRAY_ORDER = 16,       /* int32[n]: input id of each solver vertex id
                                     (0 elements when the handle is not renumbered) */
-    WBPR_ARRAY_ST = 17           /* int32[2]: solver ids of s and t (host copy) */
+    WBPR_ARRAY_ST = 17,          /* int32[2]: solver ids of s and t (host copy) */
+    WBPR_ARRAY_WARP_TIME = 18    /* uint64[grid_blocks * 8]: per warp of the last
+                                    launch's grid, ns spent in push-relabel passes
+                                    (wbpr_options.warp_time; 0 elements when off) */
 };
 wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, int64_t arg);
 wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64_t count);

@@ -36,7 +36,7 @@ ARRAY = {"height": (1, np.int32), "excess": (2, np.int64), "offsets": (3, np.int
          "bf": (8, np.int32), "in_offsets": (9, np.int64), "in_col": (10, np.int32),
          "flow_idx": (11, np.uint32), "arc2slot": (12, np.uint32), "excess_total": (13, np.int64),
          "trace": (14, np.uint64), "trace_len": (15, np.uint32), "order": (16, np.int32),
-         "st": (17, np.int32)}
+         "st": (17, np.int32), "warp_time": (18, np.uint64)}
 
 # Every function declared in include/wbpr.h.
 EXPORTED_SYMBOLS = [
@@ -65,7 +65,8 @@ class Options(ctypes.Structure):
                 ("trace", ctypes.c_int32), ("gr_ratio", ctypes.c_float),
                 ("batch_team", ctypes.c_int32), ("batch_big_slots", ctypes.c_int64),
                 ("bottom_up", ctypes.c_int32), ("bottom_up_min", ctypes.c_int32),
-                ("renumber", ctypes.c_int32)]
+                ("renumber", ctypes.c_int32), ("thread_centric", ctypes.c_int32),
+                ("warp_time", ctypes.c_int32), ("barrier_extra", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -357,7 +358,9 @@ def wbpr_export(g: Graph, what: str, count: int | None = None) -> np.ndarray:
         info = wbpr_get_info(g)
         count = {"height": info["n"], "excess": info["n"], "offsets": info["n"] + 1,
                  "in_offsets": info["n"] + 1, "arc2slot": info["m"], "excess_total": 1,
-                 "order": info["n"] if info["renumbered"] else 0, "st": 2}.get(what, info["slots"])
+                 "order": info["n"] if info["renumbered"] else 0, "st": 2,
+                 "warp_time": 8 * info["grid_blocks"] if wbpr_get_options(g).warp_time else 0}.get(
+                     what, info["slots"])
     if what == "trace":
         length = wbpr_export(g, "trace_len", 1)[0] if wbpr_get_options(g).trace > 0 else 0
         out = np.zeros(4 * int(length), dtype=dt)

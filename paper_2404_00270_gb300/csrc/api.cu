@@ -101,6 +101,9 @@ void wbpr_default_options(wbpr_options *o)
     o->bottom_up = 14;
     o->bottom_up_min = 1024;
     o->renumber = -1;
+    o->thread_centric = 0;
+    o->warp_time = 0;
+    o->barrier_extra = 0;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -146,6 +149,9 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->batch_big_slots < 0) return WBPR_EINVAL;
     if (o->bottom_up < 0 || o->bottom_up > (1 << 20) || o->bottom_up_min < 1) return WBPR_EINVAL;
     if (o->renumber < -1 || o->renumber > 1) return WBPR_EINVAL;
+    if (o->thread_centric != 0 && o->thread_centric != 1) return WBPR_EINVAL;
+    if (o->warp_time != 0 && o->warp_time != 1) return WBPR_EINVAL;
+    if (o->barrier_extra < 0 || o->barrier_extra > 1024) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -442,6 +448,13 @@ Params make_params(wbpr_graph *g, int mode)
         p.trace = g->trace;
         p.trace_cap = g->trace_cap;
     }
+    p.thread_centric = g->opts.thread_centric;
+    p.barrier_extra = g->opts.barrier_extra;
+    if (g->opts.warp_time) {
+        if (!g->warp_ns)
+            g->warp_ns = (unsigned long long *)g->alloc(sizeof(unsigned long long) * kWarps * (size_t)g->bstats_blocks, 0);
+        p.warp_ns = g->warp_ns;
+    }
     return p;
 }
 
@@ -460,6 +473,8 @@ static wbpr_status launch_solver(wbpr_graph *g, cudaStream_t st, int mode, long 
     }
     API_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st));
     API_CUDA(cudaMemsetAsync(g->bstats, 0, sizeof(long long) * (size_t)grid * kStatCount, st));
+    if (p.warp_ns)
+        API_CUDA(cudaMemsetAsync(p.warp_ns, 0, sizeof(unsigned long long) * kWarps * (size_t)grid, st));
     API_CUDA(cudaEventRecord(g->ev0, st));
     API_CUDA(solver_launch(g->layout, g->opts.small_tile, grid, p, st));
     API_CUDA(cudaEventRecord(g->ev1, st));
@@ -648,6 +663,8 @@ wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, i
         API_CUDA(cudaMemcpyAsync(&g->ctl->written_off, &keep[2], sizeof(long long), cudaMemcpyHostToDevice, st));
     }
     API_CUDA(cudaMemsetAsync(g->bstats, 0, sizeof(long long) * (size_t)grid * kStatCount, st));
+    if (p.warp_ns)
+        API_CUDA(cudaMemsetAsync(p.warp_ns, 0, sizeof(unsigned long long) * kWarps * (size_t)grid, st));
     API_CUDA(cudaEventRecord(g->ev0, st));
     API_CUDA(solver_launch(g->layout, g->opts.small_tile, grid, p, st));
     API_CUDA(cudaEventRecord(g->ev1, st));
@@ -677,6 +694,7 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
     case WBPR_ARRAY_EXCESS_TOTAL: src = &g->ctl->excess_total; elem = 8; avail = 1; break;
     case WBPR_ARRAY_TRACE_LEN: src = &g->ctl->trace_len; elem = 4; avail = 1; break;
     case WBPR_ARRAY_ORDER: src = g->order; avail = g->order ? g->n : 0; break;
+    case WBPR_ARRAY_WARP_TIME: src = g->warp_ns; elem = 8; avail = g->warp_ns ? (int64_t)kWarps * g->grid_blocks : 0; break;
     case WBPR_ARRAY_ST: {
         static_assert(sizeof(int32_t) == 4, "");
         int32_t *out = (int32_t *)host_dst;

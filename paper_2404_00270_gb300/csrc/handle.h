@@ -75,6 +75,7 @@ struct wbpr_graph {
     wbpr::Ctl *ctl = nullptr;
     long long *bstats = nullptr;
     unsigned long long *trace = nullptr;  // optional barrier trace (wbpr_options.trace)
+    unsigned long long *warp_ns = nullptr;  // optional per-warp busy time (wbpr_options.warp_time)
     int trace_cap = 0;
     int bstats_blocks = 0;
     int *edge_tmp = nullptr;           // device staging of edge flows for host outputs

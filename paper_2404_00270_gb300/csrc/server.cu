@@ -223,6 +223,7 @@ int64_t server_submit_impl(wbpr_server *s, wbpr_graph *g, int mode)
     const unsigned i = s->published[cls];
     if (i >= (unsigned)s->opts.capacity) return set_error(WBPR_ESTATE, "wbpr_server_submit: ring full");
     s->h_ring[cls][i] = make_params(g, mode);
+    s->h_ring[cls][i].warp_ns = nullptr;  // the per-warp record is zeroed only by single launches
     g->grid_blocks = cls ? s->opts.team_blocks : 1;
     s->graphs[cls].push_back(g);
     std::atomic_thread_fence(std::memory_order_release);

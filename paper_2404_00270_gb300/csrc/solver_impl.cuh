@@ -121,7 +121,7 @@ __device__ bool grid_sync(Ctx &c, int where)
     __syncthreads();
     if (threadIdx.x == 0) {
         Ctl *ctl = c.P.st.ctl;
-        c.bar_target += c.nblk;
+        c.bar_target += c.nblk + (unsigned)c.P.barrier_extra;
         __threadfence();
         if (c.nblk > 1) atomicAdd(&ctl->bar, 1ULL);
         int ok = 1;
@@ -836,12 +836,27 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
 }
 
 // Consume the AVQ of generation `gen` (step 3 of an iteration).
+// Per-warp busy time (the per-warp execution-time record of §4.3, taken by
+// the warp's first lane): from the start of a push-relabel pass to the end of
+// the warp's share of it, summed over the passes of a solve.
+__device__ __forceinline__ u64 warp_clock(const Params &P)
+{
+    return P.warp_ns && (threadIdx.x & 31) == 0 ? global_ns() : 0ull;
+}
+
+__device__ __forceinline__ void warp_clock_add(const Ctx &c, u64 t0)
+{
+    if (c.P.warp_ns && (threadIdx.x & 31) == 0)
+        c.P.warp_ns[(u64)c.bid * kWarps + (threadIdx.x >> 5)] += global_ns() - t0;
+}
+
 template <int L, int SW>
 __device__ void pr_process(Ctx &c, bool phase1, int hcap)
 {
     const Params &P = c.P;
     Ctl *ctl = P.st.ctl;
     const int gen = c.gen, s3 = gen % 3, set = gen & 1;
+    const u64 wt0 = warp_clock(P);
     reset_rotating(c, gen);
     const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
@@ -878,6 +893,58 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
             }
         }
     }
+    warp_clock_add(c, wt0);
+}
+
+// One thread-centric pass (the lock-free algorithm of Alg. 1 as the paper's
+// TC baseline runs it): every thread owns vertices tid, tid + grid, ...,
+// checks each for activity itself, and scans an active vertex's whole
+// residual list alone (a tile of one lane), then pushes or relabels.  No AVQ
+// and no degree classes: the warp waits for its longest row.  The pass
+// counts the active vertices it found (queue counter of class 0, so that an
+// empty pass ends the iterations), and applies a pending gap as the AVQ
+// compaction does, to the vertices each thread owns.
+template <int L>
+__device__ void tc_process(Ctx &c, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int n = g.n, s = g.s, t = g.t;
+    const int gen = c.gen, s3 = gen % 3;
+    const u64 wt0 = warp_clock(P);
+    // The rotating counters of generation gen - 1 (whose gap candidate is
+    // read here) are cleared after the pass's grid barrier, in iterate().
+    int gap = kUnvisited;
+    if (phase1 && P.gap) {
+        const int cand = __ldcg(&P.st.ctl->gap_level[(gen + 2) % 3]);
+        if (cand < n && __ldcg(P.st.count + cand) == 0) gap = cand;
+    }
+    const long long stride = (long long)c.nblk * kBlock;
+    const long long rounds = ((long long)n + stride - 1) / stride;  // the same for every thread
+    long long nact = 0;
+    for (long long r = 0; r < rounds; ++r) {
+        const long long v = r * stride + (long long)c.bid * kBlock + threadIdx.x;
+        int u = -1;
+        if (v < n && v != s && v != t) {
+            int hv = __ldcg(P.st.h + v);
+            if (gap != kUnvisited && hv > gap && hv < n) {
+                hv = n;
+                __stcg(P.st.h + v, n);
+            }
+            if (hv < hcap && __ldcg(P.st.e + v) > 0) u = (int)v;
+        }
+        nact += u >= 0;
+        if (P.multi_push) mp_tile<L, 1>(c, u, 0, phase1, hcap);
+        else pr_tile<L, 1>(c, u, 0, phase1, hcap);
+    }
+    const long long bn = block_sum(c, nact);
+    if (threadIdx.x == 0 && bn) {
+        atomicAdd(&P.st.ctl->q_count[s3][0], (unsigned)bn);
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)bn);
+    }
+    if (c.bid == 0 && threadIdx.x == 0 && gap != kUnvisited)
+        atomicAdd((unsigned long long *)&c.sm.stats[kStatGaps], 1ull);
+    warp_clock_add(c, wt0);
 }
 
 // Step 1 of an iteration: build the AVQ of generation `gen`.
@@ -1579,6 +1646,27 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
         // The flag names the generation whose iteration raised it, so it never
         // needs clearing (a clear could race with a slower block's read).
         if (i > 0 && P.gr_ratio > 0.f && __ldcg(&P.st.ctl->gr_due_gen) == c.gen - 1) break;
+        if (P.thread_centric) {
+            tc_process<L>(c, phase1, hcap);
+            if (c.bid == 0 && threadIdx.x == 0 && P.gr_ratio > 0.f) {
+                const u64 now = global_ns();
+                if ((float)(now - c.gr_end_ns) >= P.gr_ratio * (float)c.gr_ns) P.st.ctl->gr_due_gen = c.gen;
+            }
+            if (!grid_sync(c, 22)) return false;
+            const bool none = __ldcg(&P.st.ctl->q_count[c.gen % 3][0]) == 0;
+            reset_rotating(c, c.gen);  // every block has read generation gen - 1's gap candidate
+            c.gen++;
+            if (none) break;  // no active vertex was found: nothing was pushed
+            ++*it_total;
+            if (*it_total >= P.max_iterations) {
+                if (c.bid == 0 && threadIdx.x == 0) {
+                    atomicCAS(&P.st.ctl->err, 0, (int)WBPR_ETIMEOUT);
+                    P.st.ctl->err_where = 23;
+                }
+                return false;
+            }
+            continue;
+        }
         build_avq<L>(c, phase1, hcap);
         if (!grid_sync(c, 20)) return false;
         const unsigned tot = queue_total(P.st.ctl, c.gen);

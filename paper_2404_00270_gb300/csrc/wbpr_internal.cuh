@@ -144,6 +144,9 @@ struct Params {
     int trace_cap;               // records
     int mirror_gather;           // reset cfb[a] = cf0[rev[a]] by gather (cf and cfb may hold another
                                  // graph's state) instead of from the pair invariant
+    int thread_centric;          // 1: thread-centric iterations (one thread per vertex, no AVQ)
+    unsigned long long *warp_ns; // optional: per warp of the grid, device ns spent in push-relabel passes
+    int barrier_extra;           // tests: arrivals a grid barrier waits for beyond the grid
 };
 
 // Persistent server (solver.cu).  The rings, results, published counts and

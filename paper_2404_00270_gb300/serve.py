@@ -41,6 +41,7 @@ class Request:
     footprint: int = 0
     build_ms: float = 0.0
     device_ns: tuple | None = None  # (start, end) of the solve on the device's globaltimer
+    rejected: str | None = None     # why admission refused the request (it is not solved)
 
     @property
     def m(self) -> int:
@@ -51,6 +52,17 @@ def footprint_estimate(n: int, m: int) -> int:
     """Device bytes of a BCSR handle: 20 B per slot (at most 2 m slots),
     12 B per input arc, about 110 B per vertex of solver state."""
     return 40 * m + 12 * m + 110 * n
+
+
+def admission(need: int, in_use: int, budget: int, busy: bool) -> str:
+    """Admission decision for a request of footprint `need`: "reject" when it
+    can never fit the budget, "wait" while the requests in flight (`busy`,
+    holding `in_use` bytes) leave no room for it, else "admit"."""
+    if need > budget:
+        return "reject"
+    if busy and in_use + need > budget:
+        return "wait"
+    return "admit"
 
 
 class Server:
@@ -112,9 +124,15 @@ class Server:
                 while arrived and len(outstanding) < max_inflight:
                     req = arrived[0]
                     need = footprint_estimate(req.n, req.m)
-                    if outstanding and self.in_use + need > self.budget:
+                    verdict = admission(need, self.in_use, self.budget, bool(outstanding))
+                    if verdict == "wait":
                         break
                     arrived.popleft()
+                    if verdict == "reject":
+                        req.rejected = (f"footprint {need} B exceeds the memory budget of {self.budget} B")
+                        req.done = time.perf_counter() - t0
+                        last_progress = time.perf_counter()
+                        continue
                     tb = time.perf_counter()
                     g = wbpr_build(req.n, req.m, req.src, req.dst, req.cap, req.s, req.t, self.layout,
                                    None, build_stream)
@@ -174,6 +192,7 @@ def max_overlap(requests) -> int:
 
 
 def latency_summary(requests) -> dict:
+    requests = [r for r in requests if not getattr(r, "rejected", None)]
     lat = sorted(r.done - r.arrival for r in requests)
     n = len(lat)
     if n == 0:

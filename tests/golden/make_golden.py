@@ -16,6 +16,10 @@ Run from the repository root:
         canonical source side S* (np.packbits, bit order big), |S*|, and a
         SHA-256 of the input arrays so that a test can check that it draws
         the same graph.
+
+    python tests/golden/make_golden.py --rmat26 --dinic --scratch DIR
+        adds Dinic's value for the same graph (from the arrays in DIR) to
+        oracle_rmat26.json, an independent cross-check of the stored value.
 """
 import argparse
 import hashlib
@@ -117,6 +121,27 @@ def rmat26(scratch):
     print(json.dumps(out, indent=1))
 
 
+def rmat26_dinic(scratch):
+    """Cross-check of the stored R-MAT 26 value with Dinic's algorithm, on
+    the same drawn arrays (their SHA-256 must match the stored one)."""
+    path = os.path.join(HERE, "oracle_rmat26.json")
+    with open(path) as f:
+        out = json.load(f)
+    with open(os.path.join(scratch, "meta.json")) as f:
+        meta = json.load(f)
+    src, dst, cap = (np.load(os.path.join(scratch, k + ".npy"), mmap_mode="r") for k in ("src", "dst", "cap"))
+    if graph_sha256(src, dst, cap) != out["graph_sha256"]:
+        raise SystemExit("the drawn arrays are not the stored graph")
+    t0 = time.time()
+    ref = oracle.maxflow_dinic(meta["n"], src, dst, cap, meta["s"], meta["t"])
+    out["dinic_value"] = int(ref["value"])
+    out["dinic_wall_s"] = round(time.time() - t0, 1)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps(out, indent=1))
+
+
 def _cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
@@ -131,13 +156,18 @@ def _cpu_model() -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--rmat26", action="store_true")
+    ap.add_argument("--dinic", action="store_true",
+                    help="with --rmat26: add Dinic's value for the stored graph (drawn arrays reused)")
     ap.add_argument("--scratch", default=None, help="directory for the drawn R-MAT 26 arrays")
     a = ap.parse_args()
     if a.rmat26:
         if not a.scratch:
             raise SystemExit("--rmat26 needs --scratch DIR")
         oracle.build()
-        rmat26(a.scratch)
+        if a.dinic:
+            rmat26_dinic(a.scratch)
+        else:
+            rmat26(a.scratch)
     else:
         small()
 

@@ -1,5 +1,5 @@
 """Host logic of the serving loop that needs no GPU."""
-from paper_2404_00270_gb300.serve import footprint_estimate, latency_summary, max_overlap
+from paper_2404_00270_gb300.serve import admission, footprint_estimate, latency_summary, max_overlap
 
 
 class _R:
@@ -28,3 +28,20 @@ def test_max_overlap_of_device_intervals():
     assert max_overlap([_D(0, 10), _D(10, 20), _D(20, 30)]) == 1   # touching ends do not overlap
     assert max_overlap([_D(0, 10), _D(5, 15), _D(6, 7), _D(14, 30)]) == 3
     assert max_overlap([]) == 0
+
+
+def test_admission_rejects_what_can_never_fit():
+    assert admission(101, 0, 100, busy=False) == "reject"
+    assert admission(101, 0, 100, busy=True) == "reject"
+    assert admission(100, 0, 100, busy=False) == "admit"
+    assert admission(60, 50, 100, busy=True) == "wait"
+    assert admission(50, 50, 100, busy=True) == "admit"
+    assert admission(60, 50, 100, busy=False) == "admit"   # nothing in flight: its bytes are free again
+
+
+def test_latency_summary_skips_rejected():
+    class _X:
+        def __init__(self, a, d, rej=None):
+            self.arrival, self.done, self.rejected = a, d, rej
+    s = latency_summary([_X(0.0, 0.01), _X(0.0, 0.5, "too big")])
+    assert s["solves"] == 1 and abs(s["max_ms"] - 10.0) < 1e-9
