@@ -10,9 +10,10 @@ Run from the repository root:
         16, seed 4, capacities U[1, 10^4]; 1.07 G arcs).  The graph is drawn
         once in a child process and written to DIR as .npy files, so that the
         oracle process holds only its own residual graph (about 53 GB) while
-        the inputs stay memory-mapped.  The oracle's FIFO push-relabel runs
-        on one host core (phase 1, phase 2 and the cut BFS) and takes most of
-        an hour.  Stored: the maximum-flow value, a SHA-256 of the packed
+        the inputs stay memory-mapped.  Drawing the graph on the CPU took
+        about 12 minutes, the oracle's FIFO push-relabel on one host core
+        (phase 1, phase 2 and the cut BFS) about 18 (oracle_wall_s records
+        it).  Stored: the maximum-flow value, a SHA-256 of the packed
         canonical source side S* (np.packbits, bit order big), |S*|, and a
         SHA-256 of the input arrays so that a test can check that it draws
         the same graph.
