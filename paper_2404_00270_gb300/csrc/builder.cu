@@ -113,9 +113,10 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
 // slot_of = inclusive scan of run heads (1-based slot numbers).  Every
 // half-entry records its slot; the head of each run (one neighbour pair seen
 // from one side) writes the slot's column, sums the capacities of the run's
-// tail-side half-entries into cf0 / cf (flag 2 on int32 overflow), and writes
-// the offsets of the rows that start at its slot (rows with no slot take the
-// next row's start).  The run's head-side half-entries are the arcs col ->
+// tail-side half-entries into cf0 / cf (flag 2 on int32 overflow), and, when
+// its slot is the last of its row r, writes r's end into off[r + 1] (off is
+// zeroed before; an inclusive max-scan afterwards gives rows without slots
+// the end of the row before them).  The run's head-side half-entries are the arcs col ->
 // row, so their capacities sum to the paired slot's cf0: the pair's total
 // must fit int32 (flag 4), since a push moves residual capacity from one slot
 // to the other, and with the mirror (cfb != null) it is the initial cfb.
@@ -135,11 +136,14 @@ __global__ void merge_runs(long long len, int b, int n, const u64 *key, const un
         if (k == kp) continue;
         col[a] = (int)(k & mask);
         long long sum = 0, back = 0;
-        for (long long i = j; i < len && key[i] == k; ++i) {
+        long long i = j;
+        for (; i < len && key[i] == k; ++i) {
             const unsigned p = pos[i];
             if ((p & 1u) == 0) sum += cap[p >> 1];
             else back += cap[p >> 1];
         }
+        const long long r = (long long)(k >> b);
+        if (i == len || (long long)(key[i] >> b) != r) off[r + 1] = (long long)a + 1;
         if (sum > 0x7fffffffLL) {
             atomicOr(bad, 2);
             sum = 0;
@@ -151,63 +155,82 @@ __global__ void merge_runs(long long len, int b, int n, const u64 *key, const un
         cf0[a] = (int)sum;
         cf[a] = (int)sum;
         if (cfb) cfb[a] = (int)back;
-        const long long r = (long long)(k >> b);
-        const long long rp = j == 0 ? -1 : (long long)(kp >> b);
-        for (long long v = rp + 1; v <= r; ++v) off[v] = a;
-        if ((long long)a == S - 1)
-            for (long long v = r + 1; v <= n; ++v) off[v] = S;
     }
 }
 
-// The two half-entries of input arc i sit in mutually reverse slots;
-// arc2slot of the arc is the slot of its tail-side half-entry.  rev is null
-// when the handle keeps no reverse index (backward lookup by binary search).
+// BCSR reverse index in slot order: the head of each run (slot a) reads the
+// slot of the other half-entry of one of its arcs (position p ^ 1).
+__global__ void rev_slots(long long len, const u64 *key, const unsigned *pos, const unsigned *slot_of,
+                          const unsigned *slot_by_pos, unsigned *rev)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
+        if (j > 0 && key[j] == key[j - 1]) continue;
+        rev[slot_of[j] - 1] = slot_by_pos[pos[j] ^ 1u];
+    }
+}
+
+// arc2slot of input arc i is the slot of its tail-side half-entry.
 __global__ void pair_slots(long long m, const int *src, const int *dst, const unsigned *slot_by_pos,
-                           unsigned *rev, unsigned *arc2slot)
+                           unsigned *arc2slot)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
         if (src[i] == dst[i]) continue;  // self-loop: no slot
-        const unsigned a = slot_by_pos[2 * i];
-        if (rev) {
-            const unsigned r = slot_by_pos[2 * i + 1];
-            rev[a] = r;
-            rev[r] = a;
-        }
-        arc2slot[i] = a;
+        arc2slot[i] = slot_by_pos[2 * i];
     }
 }
 
-// Row offsets from sorted row keys: off[v] = first slot with row >= v.
-__global__ void row_offsets(long long S, int n, const u64 *key, int shift, long long *off)
+// Row ends from sorted row keys: the last slot a of row r writes off[r + 1] =
+// a + 1 (off zeroed before); the max-scan of close_offsets() then fills the
+// rows without slots.
+__global__ void row_offsets(long long S, const u64 *key, int shift, long long *off)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < S; a += stride) {
-        long long r = (long long)(key[a] >> shift);
-        long long rp = a == 0 ? -1 : (long long)(key[a - 1] >> shift);
-        for (long long v = rp + 1; v <= r; ++v) off[v] = a;
-        if (a == S - 1)
-            for (long long v = r + 1; v <= n; ++v) off[v] = S;
+        const long long r = (long long)(key[a] >> shift);
+        if (a == S - 1 || (long long)(key[a + 1] >> shift) != r) off[r + 1] = a + 1;
     }
 }
 
-// Renumbering (wbpr_options.renumber): endpoint counts per vertex, then the
-// input arcs' endpoints mapped to the new ids.  Ids are checked here, since
-// the remap indexes by them (flag 1: out of range or negative capacity).
-__global__ void count_degrees(long long m, int n, const int *src, const int *dst, const int *cap,
-                              unsigned *deg, int *bad)
+// Renumbering (wbpr_options.renumber): endpoint counts per vertex, one atomic per distinct endpoint
+// of a warp's 32 arcs (inputs often come sorted by tail, so a warp's tails
+// repeat).  Ids are checked here, since the remap indexes by them (flag 1:
+// out of range or negative capacity).  Every lane of the warp runs the same
+// number of rounds.
+__global__ void count_degrees_warp(long long m, int n, const int *src, const int *dst, const int *cap,
+                                   unsigned *deg, int *bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
-        const int u = src[i], v = dst[i];
-        if (u < 0 || u >= n || v < 0 || v >= n || cap[i] < 0) {
-            atomicOr(bad, 1);
-            continue;
+    const long long rounds = (m + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
+    for (long long q = 0; q < rounds; ++q) {
+        const long long i = q * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        int u = -1, v = -1;
+        if (i < m) {
+            u = src[i];
+            v = dst[i];
+            if (u < 0 || u >= n || v < 0 || v >= n || cap[i] < 0) {
+                atomicOr(bad, 1);
+                u = v = -1;
+            } else if (u == v) {
+                u = v = -1;
+            }
         }
-        if (u == v) continue;
-        atomicAdd(deg + u, 1u);
-        atomicAdd(deg + v, 1u);
+        const unsigned gu = __match_any_sync(0xffffffffu, u);
+        if (u >= 0 && lane == __ffs(gu) - 1) atomicAdd(deg + u, (unsigned)__popc(gu));
+        const unsigned gv = __match_any_sync(0xffffffffu, v);
+        if (v >= 0 && lane == __ffs(gv) - 1) atomicAdd(deg + v, (unsigned)__popc(gv));
     }
+}
+
+// Rows without slots take the end of the row before them: inclusive
+// max-scan over off[0..n] (off[0] = 0), in place.
+wbpr_status close_offsets_scan(long long *off, long long n, void *tmp, size_t *tmp_bytes, cudaStream_t st)
+{
+    cudaError_t e = cub::DeviceScan::InclusiveScan(tmp, *tmp_bytes, off, off, cuda::maximum<>(), (int64_t)(n + 1), st);
+    if (e != cudaSuccess) return set_error(WBPR_ECUDA, std::string("build: offsets scan: ") + cudaGetErrorString(e));
+    return WBPR_OK;
 }
 
 __global__ void iota_u32(long long len, unsigned *p)
@@ -281,11 +304,22 @@ __global__ void rcsr_in(long long mp, int b, const u64 *key_in_sorted, const uns
     }
 }
 
+// Grid of a grid-stride builder kernel: one thread per item, at most 32
+// blocks of 256 per SM of the current device.
 inline int grid_for(long long work)
 {
+    static thread_local int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = 1;
+        }
+    }
     long long b = (work + 255) / 256;
     if (b < 1) b = 1;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > 32LL * sms) b = 32LL * sms;
     return (int)b;
 }
 
@@ -388,7 +422,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_ALLOC(ids, unsigned, n, pool);
         OWN_ALLOC(g->order, int, n);
         BUILD_CUDA(cudaMemsetAsync(deg, 0, sizeof(unsigned) * (size_t)n, st));
-        count_degrees<<<grid_for(m), 256, 0, st>>>(m, (int)n, src, dst, cap, deg, bad);
+        count_degrees_warp<<<grid_for(m), 256, 0, st>>>(m, (int)n, src, dst, cap, deg, bad);
         iota_u32<<<grid_for(n), 256, 0, st>>>(n, ids);
         BUILD_CUDA(cudaGetLastError());
         BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -426,6 +460,17 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
 
     OWN_ALLOC(g->arc2slot, unsigned, m);
     OWN_ALLOC(g->off, long long, n + 1);
+    BUILD_CUDA(cudaMemsetAsync(g->off, 0, sizeof(long long) * (size_t)(n + 1), st));
+    auto close_offsets = [&](long long *o) -> wbpr_status {
+        size_t nb = 0;
+        wbpr_status r = close_offsets_scan(o, n, nullptr, &nb, st);
+        if (r != WBPR_OK) return r;
+        void *t = pool.get(nb);
+        if (!t) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+        r = close_offsets_scan(o, n, t, &nb, st);
+        pool.release(t);
+        return r;
+    };
     unsigned long long *h_maxdeg_dev = counter + 1;
     BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
 
@@ -523,7 +568,11 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, (int)n, k2s, v2s, heads, cap, (long long)S, g->col,
                                                        g->cf0, g->cf, g->cfb, g->off, slot_by_pos, bad);
             BUILD_CUDA(cudaGetLastError());
-            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->rev, g->arc2slot);
+            if (g->rev) rev_slots<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, heads, slot_by_pos, g->rev);
+            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->arc2slot);
+            BUILD_CUDA(cudaGetLastError());
+            wbpr_status rc = close_offsets(g->off);
+            if (rc != WBPR_OK) return rc;
             BUILD_CUDA(cudaGetLastError());
         } else {
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
@@ -583,8 +632,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
                                                    g->arc2slot, kin, vin);
             BUILD_CUDA(cudaGetLastError());
             BUILD_CUDA(cudaMemsetAsync(g->bf, 0, sizeof(int) * (size_t)mp, st));
-            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, ks, kb, g->off);
+            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, ks, kb, g->off);
             BUILD_CUDA(cudaGetLastError());
+            wbpr_status rc = close_offsets(g->off);
+            if (rc != WBPR_OK) return rc;
             cub::DoubleBuffer<u64> dki(kin, kinb);
             cub::DoubleBuffer<unsigned> dvi(vin, vinb);
             size_t nb = 0;
@@ -595,8 +646,11 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             pool.release(t5);
             rcsr_in<<<grid_for(mp), 256, 0, st>>>(mp, kb, dki.Current(), dvi.Current(), g->in_col, g->flow_idx);
             BUILD_CUDA(cudaGetLastError());
-            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, (int)n, dki.Current(), kb, g->in_off);
+            BUILD_CUDA(cudaMemsetAsync(g->in_off, 0, sizeof(long long) * (size_t)(n + 1), st));
+            row_offsets<<<grid_for(mp), 256, 0, st>>>(mp, dki.Current(), kb, g->in_off);
             BUILD_CUDA(cudaGetLastError());
+            rc = close_offsets(g->in_off);
+            if (rc != WBPR_OK) return rc;
         } else {
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->off, 0);
             fill_i64<<<grid_for(n + 1), 256, 0, st>>>(n + 1, g->in_off, 0);

@@ -36,7 +36,7 @@ constexpr size_t kOffDead = align256(kOffH + 4 * kMaxN);
 constexpr size_t kOffCount = align256(kOffDead + kMaxN);
 constexpr size_t kOffQ = align256(kOffCount + 4 * (kMaxN + 1));
 constexpr size_t kOffHubStart = align256(kOffQ + 6 * 4 * kMaxN);
-constexpr long long kMaxChunks = kMaxN + kMaxSlots / kChunk + 1;  // hub_chunk_entries() for BCSR
+constexpr long long kMaxChunks = hub_chunk_entries(kMaxN, kMaxSlots, kBCSR);
 constexpr size_t kOffHubChunk = align256(kOffHubStart + 2 * 4 * kMaxN);
 constexpr size_t kOffHubE0 = align256(kOffHubChunk + 2 * 4 * kMaxChunks);
 constexpr size_t kOffHubRem = align256(kOffHubE0 + 2 * 8 * kMaxN);

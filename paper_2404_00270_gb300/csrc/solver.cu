@@ -98,8 +98,14 @@ cudaError_t launch_edge_flow(int layout, long long m, const unsigned *arc2slot, 
                              int *edge_flow, cudaStream_t stream)
 {
     if (m <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
     long long blocks = (m + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > 16LL * sms) blocks = 16LL * sms;   // grid-stride: 16 blocks of 256 per SM
     edge_flow_kernel<<<(int)blocks, 256, 0, stream>>>(layout, m, arc2slot, cf0, cf, bf, prefix,
                                                       cap_in, edge_flow);
     return cudaGetLastError();

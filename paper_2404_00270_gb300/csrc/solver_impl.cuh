@@ -10,14 +10,17 @@
 // WBPR_ETIMEOUT in the control block and every block leaves the kernel.
 //
 // One iteration of Alg. 2:
-//   1. AVQ compaction: every block scans a contiguous range of vertices,
-//      stages the active ones (e > 0, h below the height cap, not s or t) in
-//      shared memory per tile class, and appends them to global queues with
-//      one atomic per class per flush (the atomic_add of Alg. 2, aggregated).
+//   1. AVQ compaction: every block scans a contiguous range of vertices and
+//      appends the active ones (e > 0, h below the height cap, not s or t) to
+//      the global queue of their tile class: warp ballots rank them, a block
+//      prefix over the warps places them, and one atomic per class per 1024
+//      vertices reserves the block's range (the atomic_add of Alg. 2,
+//      aggregated).
 //   2. grid_sync.
 //   3. Two-level parallelism: each active vertex is owned by one tile whose
 //      width follows its residual-list length: `SW` lanes (small rows), a
-//      warp, or the whole block (hub rows, taken dynamically).  The tile
+//      warp, or, for hub rows, several warps that take 256-entry chunks of the
+//      row dynamically.  The tile
 //      scans the list coalesced, gathers neighbour heights of residual arcs,
 //      and reduces (height, slot) keys to the minimum with warp shuffles;
 //      the tile's lane 0 then pushes min(e(u), cf(u,v')) with atomics when
@@ -91,6 +94,8 @@ struct Smem {
     unsigned ndfr_lo, ndfr_hi;
     unsigned qcnt[kClasses];
     unsigned qbase[kClasses];
+    unsigned wcnt[2][kWarps];    // AVQ compaction: per-warp counts of classes 0 and 1
+    unsigned gbase[2];           //                 the block's base in the global queues
     u64 red[kWarps];
     long long red64[kWarps];
     long long wsum[kWarps];
@@ -172,6 +177,13 @@ __device__ __forceinline__ long long degree(const GraphDev &g, int v)
     return d;
 }
 
+// Slots between the 16-byte boundary below a BCSR row and the row's start.
+template <int L>
+__device__ __forceinline__ int hub_lead(const GraphDev &g, int v)
+{
+    return L == kBCSR ? (int)(__ldg(g.off + v) & 3) : 0;
+}
+
 __device__ __forceinline__ int classify(const Params &P, long long d)
 {
     return d <= P.small_max ? 0 : (d <= P.warp_max ? 1 : 2);
@@ -227,34 +239,62 @@ __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
 
 // ---------------------------------------------------------------------------
 // Hub class: a vertex whose residual list is longer than warp_max is split
-// into chunks of kChunk entries.  One 64-bit atomic gives it both its queue
-// position and the id of its first chunk; the appender then records the
-// position under each of its chunk ids, so a block that takes a chunk id
-// finds its hub with one load.
+// into chunks: of kWChunk entries for a push-relabel pass (one warp each),
+// of kChunk entries for a BFS level or the cut (one block each).  One 64-bit
+// atomic gives it both its queue position and the id of its first chunk; the
+// appender then records the position under each of its chunk ids, so a warp
+// or block that takes a chunk id finds its hub with one load.  A push-relabel
+// hub's chunks start `lead` = off[u] mod 4 slots before its row (BCSR), so
+// that chunk boundaries fall on 16-byte boundaries of the slot arrays.
 // ---------------------------------------------------------------------------
 constexpr u64 kChunkMask = (1ull << 40) - 1;
 
-__device__ __forceinline__ unsigned hub_chunks(long long deg)
+__device__ __forceinline__ unsigned hub_chunks(long long deg, int chunk = kChunk, int lead = 0)
 {
-    return deg <= 0 ? 1u : (unsigned)((deg + kChunk - 1) / kChunk);
+    return deg <= 0 ? 1u : (unsigned)((deg + lead + chunk - 1) / chunk);
 }
 
-__device__ __forceinline__ void hub_append(Ctx &c, int slot3, int set, int v, long long deg, bool pr,
-                                           long long ev)
+// Appends hub v; returns its queue position, and its first chunk id and
+// chunk count in *first / *nch.  With fill = false the caller writes the
+// chunk table (warp_fill_chunks).
+__device__ __forceinline__ unsigned hub_append(Ctx &c, int slot3, int set, int v, long long deg, bool pr,
+                                               long long ev, int chunk = kChunk, int lead = 0,
+                                               bool fill = true, unsigned *first_out = nullptr,
+                                               unsigned *nch_out = nullptr)
 {
     const StateDev &st = c.P.st;
-    const unsigned nch = hub_chunks(deg);
+    const unsigned nch = hub_chunks(deg, chunk, lead);
     const u64 old = atomicAdd(&st.ctl->hub_pack[slot3], (1ull << 40) | nch);
     const unsigned pos = (unsigned)(old >> 40);
     const unsigned first = (unsigned)(old & kChunkMask);
     st.q[set][2][pos] = v;
     st.hub_start[set][pos] = first;
-    for (unsigned j = 0; j < nch; ++j) st.hub_chunk[set][first + j] = pos;
+    if (fill)
+        for (unsigned j = 0; j < nch; ++j) st.hub_chunk[set][first + j] = pos;
+    if (first_out) *first_out = first;
+    if (nch_out) *nch_out = nch;
     if (pr) {
         st.hub_e0[set][pos] = ev;
         st.hub_rem[set][pos] = ev;
         st.hub_aux[set][pos] = kNoKey;
         st.hub_done[set][pos] = 0;
+    }
+    return pos;
+}
+
+// The whole warp writes the chunk table of the hubs its lanes appended (lane
+// mask `hubs`): chunk id -> queue position, 32 entries per step.
+__device__ __forceinline__ void warp_fill_chunks(const StateDev &st, int set, unsigned hubs, unsigned pos,
+                                                 unsigned first, unsigned nch)
+{
+    const int lane = threadIdx.x & 31;
+    while (hubs) {
+        const int src = __ffs(hubs) - 1;
+        hubs &= hubs - 1;
+        const unsigned p = __shfl_sync(kFull, pos, src);
+        const unsigned f = __shfl_sync(kFull, first, src);
+        const unsigned k = __shfl_sync(kFull, nch, src);
+        for (unsigned j = lane; j < k; j += 32) st.hub_chunk[set][f + j] = p;
     }
 }
 
@@ -315,22 +355,6 @@ __device__ long long block_sum(Ctx &c, long long x)
     if (threadIdx.x == 0)
         for (int w = 0; w < kWarps; ++w) s += c.sm.red64[w];
     return s;  // valid in thread 0
-}
-
-__device__ u64 block_min(Ctx &c, u64 x)
-{
-    x = tile_min<32>(x);
-    if ((threadIdx.x & 31) == 0) c.sm.red[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        u64 y = threadIdx.x < kWarps ? c.sm.red[threadIdx.x] : kNoKey;
-        y = tile_min<32>(y);
-        if (threadIdx.x == 0) c.sm.red[0] = y;
-    }
-    __syncthreads();
-    u64 r = c.sm.red[0];
-    __syncthreads();
-    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -692,39 +716,45 @@ __device__ void mp_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
     }
 }
 
-// Block-wide inclusive scan of x; *tot receives the block total.
-__device__ __forceinline__ long long block_incl_scan(Ctx &c, long long x, long long *tot)
+// Take the next hub chunk of generation (s3, set): warp-uniform result.
+__device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks,
+                                            unsigned &pos, unsigned &j, unsigned &nch)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    x = seg_incl_scan<32>(x, lane);
-    if (lane == 31) c.sm.wsum[warp] = x;
-    __syncthreads();
-    long long before = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        long long y = c.sm.wsum[w];
-        if (w < warp) before += y;
-        all += y;
+    unsigned id = 0, lo = 0, s0 = 0, s1 = 0;
+    if ((threadIdx.x & 31) == 0) {
+        id = atomicAdd(&c.P.st.ctl->q_grab[s3], 1u);
+        if (id < nchunks) {
+            const unsigned *start = c.P.st.hub_start[set];
+            lo = __ldcg(c.P.st.hub_chunk[set] + id);  // start[lo] <= id < start[lo + 1]
+            s0 = __ldcg(start + lo);
+            s1 = lo + 1 < nh ? __ldcg(start + lo + 1) : nchunks;
+        }
     }
-    __syncthreads();
-    *tot = all;
-    return x + before;
+    id = __shfl_sync(kFull, id, 0);
+    pos = __shfl_sync(kFull, lo, 0);
+    j = id - __shfl_sync(kFull, s0, 0);
+    nch = __shfl_sync(kFull, s1, 0) - __shfl_sync(kFull, s0, 0);
+    return id < nchunks;
 }
 
-// One chunk of a hub's residual list, processed by one block.  Multi-push:
-// the chunk sums the capacity of its admissible entries, takes up to that
-// much of the hub's remaining excess with a compare-and-swap on the hub's
-// budget, and spreads what it took over its admissible entries with a block
-// prefix sum.  Single push: the chunk's minimum (height, row index) key.
-// The last chunk of the hub to finish lowers e(u) by what all chunks pushed
-// and relabels u when excess is left (or applies the single push/relabel).
+// One chunk of a hub's residual list (kWChunk entries), processed by one
+// warp: lane l holds the 8 consecutive entries 8l .. 8l + 7 of the chunk (in
+// BCSR read as two aligned 16-byte vectors of col and of cf; the chunk starts
+// `lead` slots before the row, entries outside the row are masked).
+// Multi-push: the warp sums the capacity of its admissible entries, takes up
+// to that much of the hub's remaining excess with a compare-and-swap on the
+// hub's budget, and spreads what it took over its admissible entries in slot
+// order (one warp scan of the lanes' sums).  Single push: the chunk's minimum
+// (height, row index) key.  The last chunk of the hub to finish lowers e(u)
+// by what all chunks pushed and relabels u when excess is left (or applies
+// the single push/relabel).
 template <int L>
-__device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch, bool phase1,
-                         int hcap)
+__device__ void pr_wchunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch, bool phase1, int hcap)
 {
-    constexpr int kPer = kChunk / kBlock;
+    constexpr int kPer = kWChunk / 32;
     const Params &P = c.P;
     const GraphDev &g = P.g;
+    const int lane = threadIdx.x & 31;
     const int u = __ldcg(P.st.q[set][2] + pos);
     const long long ob = __ldg(g.off + u), dout = __ldg(g.off + u + 1) - ob;
     long long ib = 0, din = 0;
@@ -733,73 +763,91 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
         din = __ldg(g.in_off + u + 1) - ib;
     }
     const long long deg = dout + din;
-    const long long r0 = (long long)j * kChunk;
-    const long long r1 = deg < r0 + kChunk ? deg : r0 + kChunk;
+    const int lead = L == kBCSR ? (int)(ob & 3) : 0;
+    const long long r0 = (long long)j * kWChunk - lead + (long long)lane * kPer;  // row index of entry 0
     const int hu = __ldcg(P.st.h + u);
-    // Multi-push: once earlier chunks have taken all of the hub's excess this
-    // chunk has nothing to push and (no excess left) no relabel to inform.
     bool spent = false;
-    if (P.multi_push) {
-        if (threadIdx.x == 0) c.sm.bcast64 = __ldcg(P.st.hub_rem[set] + pos);
-        __syncthreads();
-        spent = c.sm.bcast64 == 0;
-        __syncthreads();
-    }
+    if (P.multi_push) spent = __ldcg(P.st.hub_rem[set] + pos) == 0;
     int capv[kPer], vv[kPer], hvv[kPer];
-    long long asum = 0;
-    u64 best = kNoKey;
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-        const long long r = r0 + threadIdx.x + (long long)i * kBlock;
         capv[i] = 0;
         vv[i] = 0;
         hvv[i] = 0x7fffffff;
-        if (r < r1 && !spent) {
-            bool in;
-            const long long k = row_slot<L>(ob, dout, ib, r, in);
-            mp_load<L>(P, k, in, capv[i], vv[i], hvv[i]);
-            if (capv[i] > 0) {
-                if (hvv[i] < hu) asum += capv[i];
-                best = umin64(best, make_key(hvv[i], (unsigned)r));
+    }
+    if (!spent) {
+        const long long a0 = ob + r0;  // BCSR: absolute slot of entry 0, a multiple of 4
+        const bool vec = L == kBCSR && a0 >= 0 && a0 + kPer <= g.slots &&
+                         ((reinterpret_cast<uintptr_t>(g.col) | reinterpret_cast<uintptr_t>(g.cf)) & 15) == 0;
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < kPer / 4; ++q) {
+                const int4 cv = __ldg(reinterpret_cast<const int4 *>(g.col + a0) + q);
+                const int4 fv = __ldcg(reinterpret_cast<const int4 *>(g.cf + a0) + q);
+                vv[4 * q] = cv.x; vv[4 * q + 1] = cv.y; vv[4 * q + 2] = cv.z; vv[4 * q + 3] = cv.w;
+                capv[4 * q] = fv.x; capv[4 * q + 1] = fv.y; capv[4 * q + 2] = fv.z; capv[4 * q + 3] = fv.w;
+            }
+#pragma unroll
+            for (int i = 0; i < kPer; ++i)
+                if (r0 + i < 0 || r0 + i >= deg) capv[i] = 0;  // outside the row
+#pragma unroll
+            for (int i = 0; i < kPer; ++i)
+                if (capv[i] > 0) hvv[i] = __ldcg(P.st.h + vv[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const long long r = r0 + i;
+                if (r >= 0 && r < deg) {
+                    bool in;
+                    const long long k = row_slot<L>(ob, dout, ib, r, in);
+                    mp_load<L>(P, k, in, capv[i], vv[i], hvv[i]);
+                }
             }
         }
     }
-    if (threadIdx.x == 0 && r1 > r0 && !spent)
-        atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)(r1 - r0));
+    if (lane == 0 && !spent) {
+        const long long lo = (long long)j * kWChunk - lead, hi = lo + kWChunk;
+        const long long n_in = (hi < deg ? hi : deg) - (lo > 0 ? lo : 0);
+        if (n_in > 0) atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)n_in);
+    }
     if (!P.multi_push) {
-        best = block_min(c, best);
-        if (threadIdx.x == 0 && best != kNoKey) atomicMin(P.st.hub_aux[set] + pos, best);
+        u64 best = kNoKey;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (capv[i] > 0) best = umin64(best, make_key(hvv[i], (unsigned)(r0 + i)));
+        best = tile_min<32>(best);
+        if (lane == 0 && best != kNoKey) atomicMin(P.st.hub_aux[set] + pos, best);
     } else {
-        long long tot;
-        const long long incl = block_incl_scan(c, asum, &tot);
-        if (threadIdx.x == 0) {
-            long long take = 0;
-            if (tot > 0) {
-                long long *rp = P.st.hub_rem[set] + pos;
-                long long r = __ldcg(rp);
-                for (int tries = 0; tries < (1 << 20) && r > 0; ++tries) {
-                    const long long t = r < tot ? r : tot;
-                    const long long prev = (long long)atomicCAS((u64 *)rp, (u64)r, (u64)(r - t));
-                    if (prev == r) {
-                        take = t;
-                        break;
-                    }
-                    r = prev;
+        long long asum = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (capv[i] > 0 && hvv[i] < hu) asum += capv[i];
+        const long long incl = seg_incl_scan<32>(asum, lane);
+        const long long tot = __shfl_sync(kFull, incl, 31);
+        long long take = 0;
+        if (lane == 0 && tot > 0) {
+            long long *rp = P.st.hub_rem[set] + pos;
+            long long r = __ldcg(rp);
+            for (int tries = 0; tries < (1 << 20) && r > 0; ++tries) {
+                const long long t = r < tot ? r : tot;
+                const long long prev = (long long)atomicCAS((u64 *)rp, (u64)r, (u64)(r - t));
+                if (prev == r) {
+                    take = t;
+                    break;
                 }
+                r = prev;
             }
-            c.sm.bcast64 = take;
         }
-        __syncthreads();
-        long long budget = c.sm.bcast64 - (incl - asum);
+        take = __shfl_sync(kFull, take, 0);
+        long long budget = take - (incl - asum);
         budget = budget < 0 ? 0 : (budget > asum ? asum : budget);
         int npush = 0, hres = 0x7fffffff;
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
             int cap = capv[i];
             if (cap > 0 && hvv[i] < hu && budget > 0) {
-                const long long r = r0 + threadIdx.x + (long long)i * kBlock;
-                bool in;
-                const long long k = row_slot<L>(ob, dout, ib, r, in);
+                bool in = false;
+                const long long k = row_slot<L>(ob, dout, ib, r0 + i, in);
                 const int d = (int)(budget < cap ? budget : cap);
                 mp_push<L>(P, u, k, in, vv[i], d);
                 budget -= d;
@@ -808,16 +856,16 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
             }
             if (cap > 0 && hvv[i] < hres) hres = hvv[i];
         }
-        const u64 key = block_min(c, (u64)(unsigned)hres << 32);
-        const long long np = block_sum(c, npush);
-        if (threadIdx.x == 0) {
-            if ((int)(key >> 32) != 0x7fffffff) atomicMin(P.st.hub_aux[set] + pos, key);
-            if (np) atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], (u64)np);
+        hres = seg_min_int<32>(hres);
+        npush = seg_sum_int<32>(npush);
+        if (lane == 0) {
+            if (hres != 0x7fffffff) atomicMin(P.st.hub_aux[set] + pos, (u64)(unsigned)hres << 32);
+            if (npush) atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], (u64)npush);
         }
     }
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    if (lane == 0) {
         const unsigned done = atomicAdd(P.st.hub_done[set] + pos, 1u);
         if (done + 1 == nch) {
             __threadfence();
@@ -832,7 +880,7 @@ __device__ void pr_chunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch
             }
         }
     }
-    __syncthreads();
+    __syncwarp();
 }
 
 // Consume the AVQ of generation `gen` (step 3 of an iteration).
@@ -860,14 +908,6 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
     reset_rotating(c, gen);
     const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
-    // hub rows: chunks taken dynamically, one block each
-    {
-        const u64 hp = __ldcg(&ctl->hub_pack[s3]);
-        const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
-        unsigned pos, j, nch;
-        if (nchunks)
-            while (grab_chunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_chunk<L>(c, set, pos, j, nch, phase1, hcap);
-    }
     const int lane = threadIdx.x & 31;
     const unsigned gwarp = c.bid * kWarps + (threadIdx.x >> 5);
     const unsigned nwarps = c.nblk * kWarps;
@@ -892,6 +932,14 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
                 else pr_tile<L, SW>(c, u, sl, phase1, hcap);
             }
         }
+    }
+    // hub rows last: chunks taken dynamically, one warp each, fill the tail
+    {
+        const u64 hp = __ldcg(&ctl->hub_pack[s3]);
+        const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
+        unsigned pos, j, nch;
+        if (nchunks)
+            while (grab_wchunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap);
     }
     warp_clock_add(c, wt0);
 }
@@ -990,22 +1038,61 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
             const long long v = base + (long long)i * kBlock + threadIdx.x;
             d[i] = ev[i] > 0 ? degree<L>(g, (int)v) : 0;
         }
+        // Compaction of the active vertices of classes 0 and 1: per round a
+        // warp ballot of each class gives every lane its rank in the warp; a
+        // block prefix over the warps' counts and one global atomic per class
+        // give the block's range in the queue (Alg. 2's atomic append,
+        // aggregated over 1024 vertices).  Hubs take their chunk ids from the
+        // hub counter.
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        int cls[kAvqVerts];
+        unsigned m0[kAvqVerts], m1[kAvqVerts], w0 = 0, w1 = 0;
 #pragma unroll
         for (int i = 0; i < kAvqVerts; ++i) {
-            if (ev[i] <= 0) continue;
-            const int v = (int)(base + (long long)i * kBlock + threadIdx.x);
-            const int cls = classify(P, d[i]);
-            if (cls == 2) hub_append(c, s3, set, v, d[i], true, ev[i]);
-            else q_append(c, s3, set, cls, v);
-            ++nact;
+            cls[i] = -1;
+            unsigned hpos = 0, hfirst = 0, hn = 0;
+            if (ev[i] > 0) {
+                const int v = (int)(base + (long long)i * kBlock + threadIdx.x);
+                cls[i] = classify(P, d[i]);
+                if (cls[i] == 2)
+                    hpos = hub_append(c, s3, set, v, d[i], true, ev[i], kWChunk, hub_lead<L>(g, v), false,
+                                      &hfirst, &hn);
+                ++nact;
+            }
+            warp_fill_chunks(P.st, set, __ballot_sync(kFull, cls[i] == 2), hpos, hfirst, hn);
+            m0[i] = __ballot_sync(kFull, cls[i] == 0);
+            m1[i] = __ballot_sync(kFull, cls[i] == 1);
+            w0 += __popc(m0[i]);
+            w1 += __popc(m1[i]);
+        }
+        if (lane == 0) {
+            c.sm.wcnt[0][warp] = w0;
+            c.sm.wcnt[1][warp] = w1;
         }
         __syncthreads();
-        unsigned mx = c.sm.qcnt[0];
-        if (c.sm.qcnt[1] > mx) mx = c.sm.qcnt[1];
-        __syncthreads();  // every thread has read the counts before new appends
-        if (mx > (unsigned)(kQueueCap - kBlock * kAvqVerts)) q_flush(c, s3, set);
+        if (threadIdx.x < 2) {
+            unsigned tot = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) tot += c.sm.wcnt[threadIdx.x][w];
+            c.sm.gbase[threadIdx.x] = tot ? atomicAdd(&P.st.ctl->q_count[s3][threadIdx.x], tot) : 0u;
+        }
+        __syncthreads();
+        unsigned b0 = c.sm.gbase[0], b1 = c.sm.gbase[1];
+        for (int w = 0; w < warp; ++w) {
+            b0 += c.sm.wcnt[0][w];
+            b1 += c.sm.wcnt[1][w];
+        }
+#pragma unroll
+        for (int i = 0; i < kAvqVerts; ++i) {
+            const int v = (int)(base + (long long)i * kBlock + threadIdx.x);
+            if (cls[i] == 0) P.st.q[set][0][b0 + __popc(m0[i] & lt)] = v;
+            if (cls[i] == 1) P.st.q[set][1][b1 + __popc(m1[i] & lt)] = v;
+            b0 += __popc(m0[i]);
+            b1 += __popc(m1[i]);
+        }
+        __syncthreads();  // the counts are read before the next step writes them
     }
-    q_flush(c, s3, set);
     if (nact) atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)nact);
     if (c.bid == 0 && threadIdx.x == 0 && gap != kUnvisited)
         atomicAdd((unsigned long long *)&c.sm.stats[kStatGaps], 1ull);
@@ -1573,7 +1660,10 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
     const int base = phase1 ? 0 : n;
     const int unreach = phase1 ? n : 2 * n;
     const bool gap = phase1 && P.gap;
-    if (c.bid == 0 && threadIdx.x == 0) c.gr_start_ns = global_ns();
+    if (c.bid == 0 && threadIdx.x == 0) {
+        c.gr_start_ns = global_ns();
+        if (first_of_phase2) P.st.ctl->dead_count = 0;  // the marks are cleared below
+    }
     const long long stride = (long long)c.nblk * kBlock;
     for (long long v = c.bid * kBlock + threadIdx.x; v <= n; v += stride) {
         if (gap) __stcg(P.st.count + v, 0);
@@ -1585,15 +1675,15 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
     seed_queue<L>(c, c.gen, target);
     if (!grid_sync(c, 10)) return false;
     // Direction choice (after Beamer et al.): a level runs bottom-up when its
-    // frontier, times bottom_up, reaches the vertices not yet visited (an
-    // over-estimate: marked vertices count as unvisited) and holds at least
-    // bottom_up_min vertices.  Uniform over the team: every block reads the
-    // same counters after the barrier.  Vertices that cannot reach the target
+    // frontier, times bottom_up, reaches the vertices not yet visited (those
+    // neither reached nor marked unreachable by an earlier global relabel)
+    // and holds at least bottom_up_min vertices.  Uniform over the team: every
+    // block reads the same counters after the barrier.  Vertices that cannot reach the target
     // are marked (dead[]) and skipped by the later global relabels of the
     // phase, so bottom-up levels do not rescan their rows: no residual path
     // to the target can appear for them, because no push ever enters a
     // vertex at the height cap.
-    long long seen = 0;
+    long long seen = __ldcg(&P.st.ctl->dead_count);
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
@@ -1608,13 +1698,14 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         if (!grid_sync(c, 11)) return false;
         c.gen++;
     }
-    long long wo = 0;
+    long long wo = 0, nd = 0;
     for (long long v = c.bid * kBlock + threadIdx.x; v < n; v += stride) {
         if (v == excluded) continue;
         if (__ldcg(P.st.h + v) == kUnvisited) {
             __stcg(P.st.h + v, unreach);
             if (!P.st.dead[v]) {
                 P.st.dead[v] = 1;
+                ++nd;
                 if (phase1) wo += __ldcg(P.st.e + v);
             }
         }
@@ -1624,6 +1715,8 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         atomicAdd((u64 *)&P.st.ctl->excess_total, (u64)(-bw));
         atomicAdd((u64 *)&P.st.ctl->written_off, (u64)bw);
     }
+    const long long bd = block_sum(c, nd);
+    if (threadIdx.x == 0 && bd) atomicAdd((u64 *)&P.st.ctl->dead_count, (u64)bd);
     if (c.bid == 0 && threadIdx.x == 0) P.st.ctl->global_relabels++;
     const bool ok = grid_sync(c, 12);
     if (c.bid == 0 && threadIdx.x == 0) {
@@ -1972,6 +2065,13 @@ __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) server_kernel(ServerD
                     D.team_exit[team] = 2;
                     break;
                 }
+                // The idle limit is checked on every pass, the poller's too: a
+                // leader that keeps winning the poll token (the last one waiting)
+                // must still leave once no request has come for idle_ns.
+                if ((++spins & 63u) == 0 && global_ns() - t0 > D.idle_ns) {
+                    D.team_exit[team] = 3;
+                    break;
+                }
                 if (atomicCAS(D.poll_token, 0, 1) == 0) {
                     const unsigned st = ld_acquire_sys_u32((const unsigned *)D.stop);
                     const unsigned a0 = ld_acquire_sys_u32(D.avail[0]);
@@ -1982,11 +2082,8 @@ __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) server_kernel(ServerD
                     if (st) atomicExch((u64 *)(D.mirror + 4), 1ull);
                     __threadfence();
                     atomicExch(D.poll_token, 0);
+                    __nanosleep(200);
                     continue;
-                }
-                if ((++spins & 63u) == 0 && global_ns() - t0 > D.idle_ns) {
-                    D.team_exit[team] = 3;
-                    break;
                 }
                 __nanosleep(500);
             }

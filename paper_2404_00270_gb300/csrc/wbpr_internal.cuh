@@ -28,8 +28,13 @@ constexpr int kClasses = 3;         // tile classes: small tile, warp, block
 constexpr int kQueueCap = 1024;     // per-class shared-memory staging of queue appends
 constexpr int kUnvisited = 0x7fffffff;
 constexpr long long kRenumberAutoVertices = 1LL << 22;  // renumber = -1: on from this many vertices
-constexpr int kChunk = 2048;        // hub rows are processed in chunks of this many entries,
-                                    // one chunk per block, taken dynamically
+constexpr int kChunk = 2048;        // hub rows of a BFS level or of the cut are processed in chunks
+                                    // of this many entries, one chunk per block, taken dynamically
+#ifndef WBPR_WCHUNK
+#define WBPR_WCHUNK 256
+#endif
+constexpr int kWChunk = WBPR_WCHUNK;  // hub rows of a push-relabel pass: chunks of this many entries,
+                                      // one chunk per warp (kWChunk / 32 per lane), taken dynamically
 
 enum Layout : int { kRCSR = 0, kBCSR = 1 };
 
@@ -66,6 +71,8 @@ struct __align__(128) Ctl {
     unsigned trace_len;
     int gr_due_gen;      // time-balanced trigger: generation whose iteration made a
                          // global relabel due (-1 = none)
+    int pad2;
+    long long dead_count;    // vertices marked unreachable (dead[]) in the current phase
 };
 
 struct GraphDev {
@@ -86,11 +93,13 @@ struct GraphDev {
     const int *order;           // renumbered handle: solver id -> input id (cut side output); or null
 };
 
-// Upper bound on the hub chunks of one queue generation: every hub has at
-// most deg / kChunk + 1 chunks and the degrees sum to the residual-list entries.
-inline long long hub_chunk_entries(long long n, long long slots, int layout_tag)
+// Upper bound on the hub chunks of one queue generation: a hub of degree d
+// has at most d / kWChunk + 2 chunks (the first one may start up to 3 slots
+// before the row, so that lanes read aligned 16-byte vectors), and the
+// degrees sum to the residual-list entries.
+constexpr long long hub_chunk_entries(long long n, long long slots, int layout_tag)
 {
-    return n + (layout_tag == kRCSR ? 2 * slots : slots) / kChunk + 1;
+    return 2 * n + (layout_tag == kRCSR ? 2 * slots : slots) / kWChunk + 1;
 }
 
 struct StateDev {

@@ -62,3 +62,26 @@ def test_bipartite_shape():
     assert g.meta["max_left_degree"] == 4096
     assert (src[:lr] < nl).all() and (dst[:lr] >= nl).all()
     assert (cap == 1).all() and g.m == lr + 2 * nl
+
+
+def test_vision_grid_shape_and_closed_form():
+    """A uniform image (no noise, one block) cuts every pixel alone at
+    min(I, 255 - I) = 65, whichever intensity the block drew: no smoothness
+    arc is cut, since all pixels take the same side."""
+    import oracle
+    oracle.build()
+    for seed in (1, 2, 3):
+        g = W.vision_grid(16, 20, seed, block=32, noise=0)
+        assert g.n == 16 * 20 + 2 and (g.s, g.t) == (320, 321)
+        grid_arcs = 4 * 16 * 20 - 2 * 16 - 2 * 20
+        assert g.m == grid_arcs + 2 * 320
+        src, dst, cap = g.numpy()
+        assert ((src[grid_arcs:grid_arcs + 320] == 320) & (dst[grid_arcs + 320:] == 321)).all()
+        assert set(cap[grid_arcs:grid_arcs + 320].tolist()) <= {65, 190}
+        assert (cap[grid_arcs:grid_arcs + 320] + cap[grid_arcs + 320:] == 255).all()
+        r = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t)
+        assert r["value"] == 65 * 320
+    g = W.vision_grid(48, 40, 5, block=16)
+    src, dst, cap = g.numpy()
+    assert oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t)["value"] == \
+        oracle.maxflow_dinic(g.n, src, dst, cap, g.s, g.t)["value"]

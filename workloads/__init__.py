@@ -146,6 +146,51 @@ def grid(rows: int, cols: int, seed: int, cap_lo: int = 1, cap_hi: int = 100,
 
 
 # --------------------------------------------------------------------------
+# Vision-style segmentation network (the image-segmentation use of minimum
+# cuts the paper's §1 cites): an R x C image, pixel p = row * C + col,
+# s = R*C, t = R*C + 1.  Every pixel has a source arc s -> p with the
+# foreground term and a sink arc p -> t with the background term, and each of
+# its 4 neighbours q an arc p -> q with a smoothness capacity.  The image is a
+# seeded synthetic intensity field in integer arithmetic only: a
+# checkerboard of blocks of side `block` (bright or dark by a draw per
+# block), plus uniform noise in [-noise, noise], clamped to [0, 255].
+#   s -> p: I(p);  p -> t: 255 - I(p);  p -> q: max(1, lam - |I(p) - I(q)| / 4)
+# Arcs come in row-major pixel order, per pixel: right, left, down, up (those
+# that exist), then every s -> p, then every p -> t.
+# --------------------------------------------------------------------------
+def vision_grid(rows: int, cols: int, seed: int, block: int = 64, noise: int = 60, lam: int = 48,
+                device="cpu") -> FlowInstance:
+    dev = torch.device(device)
+    nv = rows * cols
+    pix = torch.arange(nv, device=dev, dtype=torch.int64)
+    r, c = pix // cols, pix % cols
+    nbc = (cols + block - 1) // block
+    blk = (r // block) * nbc + (c // block)
+    bright = draw_int(seed, 700, blk, 0, 1)
+    base = torch.where(bright == 1, torch.full_like(blk, 190), torch.full_like(blk, 65))
+    img = (base + draw_int(seed, 701, pix, -noise, noise)).clamp(0, 255)
+    dirs = [(0, 1), (0, -1), (1, 0), (-1, 0)]   # right, left, down, up
+    srcs, dsts, oks = [], [], []
+    for dr, dc in dirs:
+        rr, cc = r + dr, c + dc
+        ok = (rr >= 0) & (rr < rows) & (cc >= 0) & (cc < cols)
+        srcs.append(pix)
+        dsts.append((rr * cols + cc).clamp(0, nv - 1))
+        oks.append(ok)
+    src = torch.stack(srcs, 1).reshape(-1)
+    dst = torch.stack(dsts, 1).reshape(-1)
+    ok = torch.stack(oks, 1).reshape(-1)
+    src, dst = src[ok], dst[ok]
+    smooth = torch.clamp(lam - (img[src] - img[dst]).abs() // 4, min=1)
+    s, t = nv, nv + 1
+    src = torch.cat([src, torch.full((nv,), s, device=dev, dtype=torch.int64), pix])
+    dst = torch.cat([dst, pix, torch.full((nv,), t, device=dev, dtype=torch.int64)])
+    cap = torch.cat([smooth, img, 255 - img])
+    return FlowInstance(f"vision{rows}x{cols}", nv + 2, src.int(), dst.int(), cap.int(), s, t,
+                        {"rows": rows, "cols": cols, "seed": seed, "block": block, "noise": noise, "lam": lam})
+
+
+# --------------------------------------------------------------------------
 # R-MAT (Chakrabarti, Zhan, Faloutsos 2004): each of edge_factor * 2^scale
 # edges picks, at each of `scale` levels, one quadrant with probabilities
 # (a, b, c, d); quadrant b sets the destination bit, c the source bit, d both.
