@@ -450,14 +450,16 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 def batch_measure(count: int, steps: int, warmup: int, plain_sample: int, serve_count: int,
-                  serve_rates, check_oracle: bool = False) -> dict:
+                  serve_rates, tune: bool = False) -> dict:
     """The batched / served workload: `count` instances of the seeded mix of
     grids and bipartite graphs of uneven size, solved (a) one instance per
     launch on an evenly spaced sample, (b) all in one batched launch per step,
     (c) through the continuous-batching server with Poisson arrivals at
     fractions of the batched rate.  Every batched and served value must equal
-    the one-at-a-time value of the same instance (and the oracle's with
-    `check_oracle`)."""
+    the one-at-a-time value of the same instance (the oracle checks of the
+    whole mix are in tests/test_gpu_c5_mix.py).  With `tune`, the batch knobs are tuned per graph class (autotune.tune_batch),
+    the batched launch is timed again with every handle set to its class's
+    options, and the served runs use them too."""
     import numpy as np
     import torch
     import paper_2404_00270_gb300 as wb
@@ -487,14 +489,7 @@ def batch_measure(count: int, steps: int, warmup: int, plain_sample: int, serve_
         plain_vals[i] = wb.wbpr_maxflow(graphs[i], stream)
         plain_ms.append(1e3 * (time.perf_counter() - ta))
     plain_rate = len(sample) / (sum(plain_ms) / 1e3)
-    oracle_checked = 0
-    if check_oracle:
-        import oracle
-        for i in sample:
-            src, dst, cap = insts[i].numpy()
-            ref = oracle.maxflow_pr(insts[i].n, src, dst, cap, insts[i].s, insts[i].t, False, False)["value"]
-            assert ref == plain_vals[i], (i, ref, plain_vals[i])
-            oracle_checked += 1
+
     # (b) the whole mix in one batched launch per step
     for _ in range(warmup):
         vals = wb.wbpr_maxflow_batch(graphs, stream)
@@ -510,6 +505,25 @@ def batch_measure(count: int, steps: int, warmup: int, plain_sample: int, serve_
     ms = ev0.elapsed_time(ev1) / steps
     assert all(vals[i] == plain_vals[i] for i in sample)
     batch_rate = len(graphs) / (ms / 1e3)
+    tuned = {}
+    table = None
+    if tune:
+        from paper_2404_00270_gb300 import autotune
+        t0 = time.perf_counter()
+        table = autotune.tune_batch(insts, stream=stream)
+        tuned["tune_s"] = time.perf_counter() - t0
+        tuned["classes"] = len(table.entries)
+        autotune.apply_table(graphs, table)
+        vals_t = wb.wbpr_maxflow_batch(graphs, stream)
+        assert list(vals_t) == list(vals)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            vals_t = wb.wbpr_maxflow_batch(graphs, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        tuned["batched_solves_per_s"] = len(graphs) / (ev0.elapsed_time(ev1) / steps / 1e3)
+        tuned["speedup_vs_default_batch"] = tuned["batched_solves_per_s"] / batch_rate
     inst_ms = [wb.wbpr_get_stats(G)["solve_ms"] for G in graphs]
     slowest = sorted(range(len(graphs)), key=lambda i: -inst_ms[i])[:5]
     slowest = [{"spec": list(specs[i]), "ms": inst_ms[i], "team_blocks": wb.wbpr_get_info(graphs[i])["grid_blocks"]}
@@ -529,7 +543,7 @@ def batch_measure(count: int, steps: int, warmup: int, plain_sample: int, serve_
         reqs = [serve.Request(i, g.n, g.src, g.dst, g.cap, g.s, g.t, float(a))
                 for i, (g, a) in enumerate(zip(insts[:n_serve], arrivals))]
         free_b, _ = torch.cuda.mem_get_info()
-        srv = serve.Server(int(0.5 * free_b))
+        srv = serve.Server(int(0.5 * free_b), table=table)
         out = srv.run(reqs)
         bad = [r.rid for r in out if r.value != batch_vals[r.rid]]
         assert not bad, bad
@@ -541,8 +555,8 @@ def batch_measure(count: int, steps: int, warmup: int, plain_sample: int, serve_
             "plain_solves_per_s": plain_rate, "plain_sample": len(sample),
             "plain_p50_ms": float(np.percentile(plain_ms, 50)),
             "plain_p99_ms": float(np.percentile(plain_ms, 99)),
-            "speedup_vs_plain": batch_rate / plain_rate, "oracle_checked": oracle_checked,
-            "slowest_in_batch": slowest, "serving": serving}
+            "speedup_vs_plain": batch_rate / plain_rate,
+            "tuned": tuned, "slowest_in_batch": slowest, "serving": serving}
 
 
 def run_batch(args):
@@ -551,7 +565,7 @@ def run_batch(args):
     sampler = ClockSampler(0)
     sampler.start()
     res = batch_measure(args.batch_count, args.steps, args.warmup, args.plain_sample, args.serve_count,
-                        args.serve_rates)
+                        args.serve_rates, tune=args.tune)
     clocks = sampler.stop()
     line = {
         "metric": f"batched solves/s ({res['instances']:,}-instance mix, one batched launch)",
@@ -651,6 +665,7 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=512)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0])
+    ap.add_argument("--tune", action="store_true", help="batch: per-class tuned knobs, timed again")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

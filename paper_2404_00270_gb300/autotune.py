@@ -8,6 +8,11 @@ phase-1 solves of one graph under a grid of candidates, checks that every
 candidate finds the same flow value, and keeps the fastest.  Results are
 stored in a JSON table keyed by a coarse graph class (size, mean degree and
 hub skew), so later graphs of the same class start from the tuned options.
+
+For batches (wbpr_maxflow_batch and the server) tune_batch() times each
+class's largest instance the way the batch solves it (one block, or a team
+of blocks for large instances) and apply_table() sets every handle of a
+batch to its class's entry before the batched launch.
 """
 from __future__ import annotations
 
@@ -16,7 +21,7 @@ import json
 import math
 import os
 
-from . import (Options, WBPR_BCSR, wbpr_build, wbpr_default_options, wbpr_get_info,
+from . import (Options, WBPR_BCSR, wbpr_build, wbpr_default_options, wbpr_get_info, wbpr_get_options,
                wbpr_get_stats, wbpr_maxflow, wbpr_set_options)
 
 KNOBS = ("small_tile", "small_max_degree", "warp_max_degree", "grid_blocks", "gr_ratio", "bottom_up")
@@ -74,6 +79,62 @@ def autotune(n, m, src, dst, cap, s, t, layout=WBPR_BCSR, reps: int = 2, limit: 
         return trials[0][0], trials[0][1], trials
     finally:
         g.close()
+
+
+def batch_candidates():
+    """Knobs a batched solve can vary per instance (the server kernel's tile
+    width is fixed at 8 lanes, and the team size is the batch's)."""
+    for wmax, ratio, bu in itertools.product([256, 1024], [0.5, 1.0, 2.0, 4.0], [14, 0]):
+        yield {"warp_max_degree": wmax, "gr_ratio": ratio, "bottom_up": bu}
+
+
+def tune_batch(instances, layout=WBPR_BCSR, team: int = 16, big_slots: int = 1 << 15, reps: int = 1,
+               stream=None, table: "Table | None" = None):
+    """Tunes the batch knobs per graph class.  For every class among
+    `instances` (objects with n, m, src, dst, cap, s, t), its largest
+    instance is solved as a batch solves it -- on a grid of one block, or of
+    `team` blocks when it has more than `big_slots` residual slots -- under
+    every batch candidate; the fastest is recorded.  Returns the table."""
+    table = table or Table()
+    reps_by_class = {}
+    for inst in instances:
+        g = wbpr_build(inst.n, inst.m, inst.src, inst.dst, inst.cap, inst.s, inst.t, layout, None, stream)
+        info = wbpr_get_info(g)
+        g.close()
+        key = graph_class(info["n"], info["slots"], info["max_degree"])
+        if key not in reps_by_class or info["slots"] > reps_by_class[key][1]:
+            reps_by_class[key] = (inst, info["slots"])
+    for key, (inst, slots) in sorted(reps_by_class.items()):
+        blocks = team if slots > big_slots else 1
+        g = wbpr_build(inst.n, inst.m, inst.src, inst.dst, inst.cap, inst.s, inst.t, layout, None, stream)
+        try:
+            value = None
+            for cfg in batch_candidates():
+                o = _apply(wbpr_default_options(), cfg)
+                o.grid_blocks = blocks
+                wbpr_set_options(g, o)
+                best = math.inf
+                for _ in range(reps):
+                    v = wbpr_maxflow(g, stream)
+                    if value is None:
+                        value = v
+                    elif v != value:
+                        raise RuntimeError(f"candidate {cfg} found flow {v}, another found {value}")
+                    best = min(best, wbpr_get_stats(g)["solve_ms"])
+                table.record(key, cfg, best)
+        finally:
+            g.close()
+    return table
+
+
+def apply_table(graphs, table: "Table"):
+    """Sets every handle's options to its class's tuned knobs (unknown
+    classes keep theirs)."""
+    for g in graphs:
+        info = wbpr_get_info(g)
+        e = table.entries.get(graph_class(info["n"], info["slots"], info["max_degree"]))
+        if e:
+            wbpr_set_options(g, _apply(wbpr_get_options(g), e["options"]))
 
 
 class Table:

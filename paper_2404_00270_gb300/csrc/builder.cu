@@ -16,6 +16,7 @@
 // only as many passes as the vertex count needs.  Sorting and scans use CUB
 // (device radix sort / scan, header-only).
 #include <cub/cub.cuh>
+#include <thrust/iterator/transform_iterator.h>
 
 #include <stdint.h>
 
@@ -84,15 +85,23 @@ __global__ void half_keys(long long m, int n, int b, u64 loop_key, const int *sr
     if (threadIdx.x == 0 && local) atomicAdd(nonloop, local);
 }
 
-// Capacity of each sorted half-entry's arc on its tail side, 0 on its head side.
-__global__ void tail_caps(long long len, const unsigned *pos, const int *cap, int *out)
+// Capacity of each sorted half-entry's arc, in sorted order: c on its tail
+// side, -(c + 1) on its head side (c >= 0), so that later passes read both
+// sums of a run sequentially instead of gathering cap[] again.
+__global__ void sorted_caps(long long len, const unsigned *pos, const int *cap, int *out)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
         const unsigned p = pos[j];
-        out[j] = (p & 1u) ? 0 : cap[p >> 1];
+        const int c = cap[p >> 1];
+        out[j] = (p & 1u) ? -c - 1 : c;
     }
 }
+
+// The tail-side capacity of a sorted_caps() entry (0 on the head side).
+struct TailPart {
+    __host__ __device__ int operator()(int x) const { return x > 0 ? x : 0; }
+};
 
 __global__ void scatter_prefix(long long len, const unsigned *pos, const int *pre, int *prefix)
 {
@@ -122,8 +131,8 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
 // to the other, and with the mirror (cfb != null) it is the initial cfb.
 // Runs are short: one per (u, v), as long as the number of duplicate arcs
 // between u and v.
-__global__ void merge_runs(long long len, int b, int n, const u64 *key, const unsigned *pos, const unsigned *slot_of,
-                           const int *cap, long long S, int *col, int *cf0, int *cf, int *cfb, long long *off,
+__global__ void merge_runs(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
+                           const int *cj, int *col, int *cf0, int *cf, int *cfb, long long *off,
                            unsigned *slot_by_pos, int *bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -138,9 +147,9 @@ __global__ void merge_runs(long long len, int b, int n, const u64 *key, const un
         long long sum = 0, back = 0;
         long long i = j;
         for (; i < len && key[i] == k; ++i) {
-            const unsigned p = pos[i];
-            if ((p & 1u) == 0) sum += cap[p >> 1];
-            else back += cap[p >> 1];
+            const int x = cj[i];
+            if (x >= 0) sum += x;
+            else back += -(long long)x - 1;
         }
         const long long r = (long long)(k >> b);
         if (i == len || (long long)(key[i] >> b) != r) off[r + 1] = (long long)a + 1;
@@ -516,24 +525,25 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         OWN_ALLOC(g->cap_in, int, m);
         if (m > 0) BUILD_CUDA(cudaMemcpyAsync(g->cap_in, cap, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st));
         BUILD_CUDA(cudaMemsetAsync(g->prefix, 0, sizeof(int) * (size_t)(m > 0 ? m : 1), st));
+        int *cj = nullptr;
         if (len > 0) {
-            int *tail_cap, *pre;
-            BUILD_ALLOC(tail_cap, int, len, pool);
+            int *pre;
+            BUILD_ALLOC(cj, int, len, pool);
             BUILD_ALLOC(pre, int, len, pool);
-            tail_caps<<<grid_for(len), 256, 0, st>>>(len, v2s, cap, tail_cap);
+            sorted_caps<<<grid_for(len), 256, 0, st>>>(len, v2s, cap, cj);
             BUILD_CUDA(cudaGetLastError());
+            auto tails = thrust::make_transform_iterator(cj, TailPart());
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, k2s, tail_cap, pre, (int64_t)len,
+            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, k2s, tails, pre, (int64_t)len,
                                                           cuda::std::equal_to<>(), st));
             void *t2 = pool.get(nb);
             if (!t2) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, k2s, tail_cap, pre, (int64_t)len,
+            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, k2s, tails, pre, (int64_t)len,
                                                           cuda::std::equal_to<>(), st));
             pool.release(t2);
             scatter_prefix<<<grid_for(len), 256, 0, st>>>(len, v2s, pre, g->prefix);
             BUILD_CUDA(cudaGetLastError());
             pool.release(pre);
-            pool.release(tail_cap);
         }
 
         // ---- merge runs into slots ------------------------------------------------
@@ -565,9 +575,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             OWN_ALLOC(g->cfb, int, S);
         }
         if (S > 0) {
-            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, (int)n, k2s, v2s, heads, cap, (long long)S, g->col,
-                                                       g->cf0, g->cf, g->cfb, g->off, slot_by_pos, bad);
+            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cj, g->col, g->cf0, g->cf, g->cfb,
+                                                       g->off, slot_by_pos, bad);
             BUILD_CUDA(cudaGetLastError());
+            pool.release(cj);
             if (g->rev) rev_slots<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, heads, slot_by_pos, g->rev);
             pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->arc2slot);
             BUILD_CUDA(cudaGetLastError());

@@ -298,6 +298,44 @@ __device__ __forceinline__ void warp_fill_chunks(const StateDev &st, int set, un
     }
 }
 
+// Hub appends of a whole warp (all lanes call, `is_hub` on the lanes that
+// append): one atomic on the hub counter for all of the warp's hubs, their
+// queue positions by rank and their first chunk ids by a warp scan of their
+// chunk counts (kWChunk entries, BCSR rows aligned down to 16 bytes), then
+// the warp writes their chunk tables together.
+template <int L>
+__device__ __forceinline__ void warp_hub_append(Ctx &c, int slot3, int set, bool is_hub, int v, long long deg,
+                                                long long ev)
+{
+    const unsigned hm = __ballot_sync(kFull, is_hub);
+    if (!hm) return;
+    const StateDev &st = c.P.st;
+    const int lane = threadIdx.x & 31;
+    const unsigned nch = is_hub ? hub_chunks(deg, kWChunk, hub_lead<L>(c.P.g, v)) : 0u;
+    unsigned incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned tot = __shfl_sync(kFull, incl, 31);
+    u64 base = 0;
+    if (lane == 0) base = atomicAdd(&st.ctl->hub_pack[slot3], ((u64)__popc(hm) << 40) | tot);
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned pos = (unsigned)(base >> 40) + __popc(hm & ((1u << lane) - 1u));
+    const unsigned first = (unsigned)(base & kChunkMask) + incl - nch;
+    if (is_hub) {
+        st.q[set][2][pos] = v;
+        st.hub_start[set][pos] = first;
+        st.hub_e0[set][pos] = ev;
+        st.hub_rem[set][pos] = ev;
+        st.hub_aux[set][pos] = kNoKey;
+        st.hub_done[set][pos] = 0;
+    }
+    warp_fill_chunks(st, set, hm, pos, first, nch);
+}
+
+
 __device__ __forceinline__ unsigned queue_total(const Ctl *ctl, int gen)
 {
     const int s3 = gen % 3;
@@ -1009,14 +1047,16 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
         int cand = __ldcg(&P.st.ctl->gap_level[(gen + 2) % 3]);
         if (cand < n && __ldcg(P.st.count + cand) == 0) gap = cand;
     }
-    const long long chunk = ((long long)n + c.nblk - 1) / c.nblk;
-    const long long v0 = chunk * c.bid;
-    const long long v1 = v0 + chunk < n ? v0 + chunk : n;
     // kAvqVerts vertices per thread per step, their loads issued together
-    // (heights, then excesses, then row offsets of the active ones).
+    // (heights, then excesses, then row offsets of the active ones).  The
+    // blocks take the steps of kBlock * kAvqVerts vertices in turn, so that a
+    // run of long rows (a renumbered graph puts its hubs first) is spread
+    // over many blocks.
     constexpr int kAvqVerts = 4;
+    constexpr long long kStep = (long long)kBlock * kAvqVerts;
     long long nact = 0;
-    for (long long base = v0; base < v1; base += (long long)kBlock * kAvqVerts) {
+    const long long v1 = n;
+    for (long long base = (long long)c.bid * kStep; base < n; base += (long long)c.nblk * kStep) {
         int hv[kAvqVerts];
         long long ev[kAvqVerts], d[kAvqVerts];
 #pragma unroll
@@ -1051,16 +1091,12 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
 #pragma unroll
         for (int i = 0; i < kAvqVerts; ++i) {
             cls[i] = -1;
-            unsigned hpos = 0, hfirst = 0, hn = 0;
             if (ev[i] > 0) {
-                const int v = (int)(base + (long long)i * kBlock + threadIdx.x);
                 cls[i] = classify(P, d[i]);
-                if (cls[i] == 2)
-                    hpos = hub_append(c, s3, set, v, d[i], true, ev[i], kWChunk, hub_lead<L>(g, v), false,
-                                      &hfirst, &hn);
                 ++nact;
             }
-            warp_fill_chunks(P.st, set, __ballot_sync(kFull, cls[i] == 2), hpos, hfirst, hn);
+            const int v = (int)(base + (long long)i * kBlock + threadIdx.x);
+            warp_hub_append<L>(c, s3, set, cls[i] == 2, v, d[i], ev[i]);
             m0[i] = __ballot_sync(kFull, cls[i] == 0);
             m1[i] = __ballot_sync(kFull, cls[i] == 1);
             w0 += __popc(m0[i]);

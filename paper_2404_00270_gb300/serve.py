@@ -70,8 +70,9 @@ class Server:
 
     def __init__(self, memory_budget: int, layout: int = WBPR_BCSR, big_slots: int = 1 << 15,
                  team_blocks: int = 8, big_teams: int | None = None, small_blocks: int | None = None,
-                 idle_ms: int = 60000, device=None):
+                 idle_ms: int = 60000, device=None, table=None):
         load()
+        self.table = table   # autotune.Table: per-class options for each request's handle
         self.device = torch.device(device or "cuda", torch.cuda.current_device())
         self.budget = int(memory_budget)
         self.layout = layout
@@ -137,6 +138,9 @@ class Server:
                     g = wbpr_build(req.n, req.m, req.src, req.dst, req.cap, req.s, req.t, self.layout,
                                    None, build_stream)
                     req.build_ms = 1e3 * (time.perf_counter() - tb)
+                    if self.table is not None:
+                        from .autotune import apply_table
+                        apply_table([g], self.table)
                     req.footprint = max(need, wbpr_get_info(g)["device_bytes"])
                     self.in_use += req.footprint
                     self.peak_in_use = max(self.peak_in_use, self.in_use)

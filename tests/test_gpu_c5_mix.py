@@ -19,7 +19,7 @@ import workloads as W
 from tests.gpu_helpers import wb
 from tests.oracle_pool import spec_values
 
-pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+pytestmark = pytest.mark.gpu
 
 
 def _selection():
@@ -31,6 +31,7 @@ def _selection():
     return [specs[i] for i in idx]
 
 
+@pytest.mark.slow
 def test_c5_mix_batched_and_served_equal_oracle():
     m = wb()
     from paper_2404_00270_gb300 import serve
@@ -65,3 +66,47 @@ def test_c5_mix_batched_and_served_equal_oracle():
     print(f"C5 mix, {len(insts)} instances: batched {rate:.0f} solves/s; served {summ['solves_per_s']:.0f} "
           f"solves/s, p50 {summ['p50_ms']:.0f} ms, p99 {summ['p99_ms']:.0f} ms, "
           f"up to {summ['max_concurrent_on_device']} solves at once on the device")
+
+
+@pytest.mark.slow
+def test_c5_full_stream_batched_equals_oracle():
+    """All 4,096 instances of the stated stream in one batched launch."""
+    m = wb()
+    specs = W.batch_spec(4096)
+    refs = spec_values(specs)
+    dev = torch.device("cuda:0")
+    graphs = []
+    for sp in specs:
+        g = W.make_from_spec(sp, device=dev)
+        graphs.append(m.wbpr_build(g.n, g.m, g.src, g.dst, g.cap, g.s, g.t, m.WBPR_BCSR))
+        del g
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    values = m.wbpr_maxflow_batch(graphs)
+    ev1.record()
+    torch.cuda.synchronize()
+    for G in graphs:
+        G.close()
+    bad = [i for i, (a, b) in enumerate(zip(values, refs)) if a != b]
+    assert not bad, bad[:10]
+    print(f"C5 stream, 4096 instances in one batched launch: {ev0.elapsed_time(ev1):.0f} ms")
+
+
+def test_batch_with_tuned_table_keeps_values():
+    """Per-class tuned knobs (autotune.tune_batch) change no value."""
+    m = wb()
+    from paper_2404_00270_gb300 import autotune
+    specs = W.batch_spec(48, base_seed=7000, grid_hi=96, bip_hi=1 << 13)
+    refs = spec_values(specs)
+    insts = [W.make_from_spec(sp, device="cuda:0") for sp in specs]
+    table = autotune.tune_batch(insts, team=4, big_slots=1 << 13)
+    assert table.entries
+    graphs = [m.wbpr_build(g.n, g.m, g.src, g.dst, g.cap, g.s, g.t, m.WBPR_BCSR) for g in insts]
+    autotune.apply_table(graphs, table)
+    o = m.wbpr_get_options(graphs[0])
+    o.batch_team, o.batch_big_slots = 4, 1 << 13
+    m.wbpr_set_options(graphs[0], o)
+    assert m.wbpr_maxflow_batch(graphs) == refs
+    for G in graphs:
+        G.close()
