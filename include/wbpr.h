@@ -121,6 +121,10 @@ typedef struct wbpr_options {
                                  spent in push-relabel passes (taken by the warp's
                                  first lane, summed over the solve); read with
                                  wbpr_export(WBPR_ARRAY_WARP_TIME).  Default 0. */
+    int32_t stage_hubs;       /* 1 = stage the residual-list chunks of hub rows in shared
+                                 memory: a warp copies its next chunk (cp.async) while
+                                 it works on the current one (BCSR; 32 KB of shared
+                                 memory per block).  0 = read them directly. */
     int32_t barrier_extra;    /* for tests of the device wait limit only: every grid
                                  barrier waits for this many arrivals more than the
                                  grid has, so its wait runs out after

@@ -103,6 +103,7 @@ void wbpr_default_options(wbpr_options *o)
     o->renumber = -1;
     o->thread_centric = 0;
     o->warp_time = 0;
+    o->stage_hubs = 1;
     o->barrier_extra = 0;
 }
 
@@ -152,6 +153,7 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->thread_centric != 0 && o->thread_centric != 1) return WBPR_EINVAL;
     if (o->warp_time != 0 && o->warp_time != 1) return WBPR_EINVAL;
     if (o->barrier_extra < 0 || o->barrier_extra > 1024) return WBPR_EINVAL;
+    if (o->stage_hubs != 0 && o->stage_hubs != 1) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -372,10 +374,17 @@ static int auto_cycle(const wbpr_graph *g)
     return g->opts.gr_ratio > 0.f ? 1000 : 16;
 }
 
+// Dynamic shared memory of a solver launch: the hub-chunk stage (BCSR).
+static size_t launch_smem(const wbpr_graph *g)
+{
+    return g->opts.stage_hubs && g->layout == WBPR_BCSR ? (size_t)kStageBytes : 0;
+}
+
 static int choose_grid(wbpr_graph *g)
 {
     int per_sm = 0;
-    if (solver_max_blocks_per_sm(g->layout, g->opts.small_tile, &per_sm) != cudaSuccess || per_sm < 1) {
+    if (solver_max_blocks_per_sm(g->layout, g->opts.small_tile, &per_sm, launch_smem(g)) != cudaSuccess ||
+        per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -476,7 +485,7 @@ static wbpr_status launch_solver(wbpr_graph *g, cudaStream_t st, int mode, long 
     if (p.warp_ns)
         API_CUDA(cudaMemsetAsync(p.warp_ns, 0, sizeof(unsigned long long) * kWarps * (size_t)grid, st));
     API_CUDA(cudaEventRecord(g->ev0, st));
-    API_CUDA(solver_launch(g->layout, g->opts.small_tile, grid, p, st));
+    API_CUDA(solver_launch(g->layout, g->opts.small_tile, grid, p, st, launch_smem(g)));
     API_CUDA(cudaEventRecord(g->ev1, st));
     return WBPR_OK;
 }
@@ -666,7 +675,7 @@ wbpr_status wbpr_run_stage(wbpr_graph *g, wbpr_stream_t stream, int32_t stage, i
     if (p.warp_ns)
         API_CUDA(cudaMemsetAsync(p.warp_ns, 0, sizeof(unsigned long long) * kWarps * (size_t)grid, st));
     API_CUDA(cudaEventRecord(g->ev0, st));
-    API_CUDA(solver_launch(g->layout, g->opts.small_tile, grid, p, st));
+    API_CUDA(solver_launch(g->layout, g->opts.small_tile, grid, p, st, launch_smem(g)));
     API_CUDA(cudaEventRecord(g->ev1, st));
     g->solved_flow = g->solved_value = false;
     return collect(g, st, false);

@@ -78,19 +78,31 @@ static void *pick_kernel(int layout, int small_tile)
     return solve_kernel_rcsr_8();
 }
 
-cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks)
+// A launch with the hub-chunk stage needs 4 x (static + 32 KB) of shared
+// memory per SM: ask for a carveout that holds it (else the default split).
+static cudaError_t set_carveout(void *kernel, size_t dyn_smem)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pick_kernel(layout, small_tile),
-                                                         kBlock, 0);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                dyn_smem ? 90 : (int)cudaSharedmemCarveoutDefault);
+}
+
+cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks, size_t dyn_smem)
+{
+    void *k = pick_kernel(layout, small_tile);
+    cudaError_t e = set_carveout(k, dyn_smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kBlock, dyn_smem);
 }
 
 cudaError_t solver_launch(int layout, int small_tile, int grid, const Params &p,
-                          cudaStream_t stream)
+                          cudaStream_t stream, size_t dyn_smem)
 {
     Params local = p;
     void *args[] = {&local};
-    return cudaLaunchCooperativeKernel(pick_kernel(layout, small_tile), dim3(grid), dim3(kBlock),
-                                       args, 0, stream);
+    void *k = pick_kernel(layout, small_tile);
+    cudaError_t e = set_carveout(k, dyn_smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kBlock), args, dyn_smem, stream);
 }
 
 cudaError_t launch_edge_flow(int layout, long long m, const unsigned *arc2slot, const int *cf0,

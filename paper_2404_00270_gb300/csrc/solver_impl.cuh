@@ -118,7 +118,26 @@ struct Ctx {
     unsigned nblk;
     unsigned bid;
     u64 gr_start_ns, gr_ns, gr_end_ns;  // last global relabel (rank 0, thread 0)
+    int *stage;      // dynamic shared memory for staging hub chunks (kStageBytes), or null
 };
+
+// Asynchronous 16-byte copies global -> shared (cp.async, L2 only), and the
+// waits for them: hardware waits on the thread's own copy groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
+{
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
 
 // Grid-wide barrier with a time limit.  Returns false on any device error.
 __device__ bool grid_sync(Ctx &c, int where)
@@ -192,14 +211,29 @@ __device__ __forceinline__ int classify(const Params &P, long long d)
 // ---------------------------------------------------------------------------
 // Queue production: stage in shared memory, flush with one atomic per class.
 // ---------------------------------------------------------------------------
+// The lanes of a warp that append at the same time and to the same class
+// share one atomic (opportunistic aggregation: whatever lanes are converged
+// here); once the block's staging is full, the overflow goes to the global
+// queue, again with one atomic per group of lanes.
 __device__ __forceinline__ void q_append(Ctx &c, int slot3, int set, int cls, int v)
 {
-    unsigned pos = atomicAdd(&c.sm.qcnt[cls], 1u);
+    const unsigned am = __activemask();
+    const unsigned same = __match_any_sync(am, cls);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(same) - 1;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&c.sm.qcnt[cls], (unsigned)__popc(same));
+    const unsigned pos = __shfl_sync(same, base, leader) + __popc(same & lt);
+    const unsigned ov = __ballot_sync(same, pos >= (unsigned)kQueueCap);
     if (pos < (unsigned)kQueueCap) {
         c.sm.qbuf[cls][pos] = v;
     } else {
-        unsigned gpos = atomicAdd(&c.P.st.ctl->q_count[slot3][cls], 1u);
-        c.P.st.q[set][cls][gpos] = v;
+        const int l2 = __ffs(ov) - 1;
+        unsigned gbase = 0;
+        if (lane == l2) gbase = atomicAdd(&c.P.st.ctl->q_count[slot3][cls], (unsigned)__popc(ov));
+        gbase = __shfl_sync(ov, gbase, l2);
+        c.P.st.q[set][cls][gbase + __popc(ov & lt)] = v;
     }
 }
 
@@ -775,6 +809,30 @@ __device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh
     return id < nchunks;
 }
 
+// Starts the copies of this lane's 8 entries of hub chunk (pos, j) into the
+// stage `buf` (neighbour ids at lane * 8, capacities at kWChunk + lane * 8);
+// false (nothing copied) where pr_wchunk would not read them as vectors.
+template <int L>
+__device__ __forceinline__ bool stage_wchunk(Ctx &c, int set, unsigned pos, unsigned j, int *buf)
+{
+    constexpr int kPer = kWChunk / 32;
+    const GraphDev &g = c.P.g;
+    const int lane = threadIdx.x & 31;
+    const int u = __ldcg(c.P.st.q[set][2] + pos);
+    const long long ob = __ldg(g.off + u);
+    const long long a0 = (ob & ~3LL) + (long long)j * kWChunk + (long long)lane * kPer;
+    const bool ok = L == kBCSR && a0 >= 0 && a0 + kPer <= g.slots &&
+                    ((reinterpret_cast<uintptr_t>(g.col) | reinterpret_cast<uintptr_t>(g.cf)) & 15) == 0;
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < kPer / 4; ++q) {
+            cp_async16(buf + lane * kPer + 4 * q, g.col + a0 + 4 * q);
+            cp_async16(buf + kWChunk + lane * kPer + 4 * q, g.cf + a0 + 4 * q);
+        }
+    }
+    return ok;
+}
+
 // One chunk of a hub's residual list (kWChunk entries), processed by one
 // warp: lane l holds the 8 consecutive entries 8l .. 8l + 7 of the chunk (in
 // BCSR read as two aligned 16-byte vectors of col and of cf; the chunk starts
@@ -787,7 +845,8 @@ __device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh
 // by what all chunks pushed and relabels u when excess is left (or applies
 // the single push/relabel).
 template <int L>
-__device__ void pr_wchunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch, bool phase1, int hcap)
+__device__ void pr_wchunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch, bool phase1, int hcap,
+                          const int *staged = nullptr)
 {
     constexpr int kPer = kWChunk / 32;
     const Params &P = c.P;
@@ -818,10 +877,14 @@ __device__ void pr_wchunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nc
         const bool vec = L == kBCSR && a0 >= 0 && a0 + kPer <= g.slots &&
                          ((reinterpret_cast<uintptr_t>(g.col) | reinterpret_cast<uintptr_t>(g.cf)) & 15) == 0;
         if (vec) {
+            // this lane's entries: from its stage (copied while the warp worked on
+            // the previous chunk), else from global memory
+            const int4 *sc = staged ? reinterpret_cast<const int4 *>(staged + lane * kPer) : nullptr;
+            const int4 *sf = staged ? reinterpret_cast<const int4 *>(staged + kWChunk + lane * kPer) : nullptr;
 #pragma unroll
             for (int q = 0; q < kPer / 4; ++q) {
-                const int4 cv = __ldg(reinterpret_cast<const int4 *>(g.col + a0) + q);
-                const int4 fv = __ldcg(reinterpret_cast<const int4 *>(g.cf + a0) + q);
+                const int4 cv = sc ? sc[q] : __ldg(reinterpret_cast<const int4 *>(g.col + a0) + q);
+                const int4 fv = sf ? sf[q] : __ldcg(reinterpret_cast<const int4 *>(g.cf + a0) + q);
                 vv[4 * q] = cv.x; vv[4 * q + 1] = cv.y; vv[4 * q + 2] = cv.z; vv[4 * q + 3] = cv.w;
                 capv[4 * q] = fv.x; capv[4 * q + 1] = fv.y; capv[4 * q + 2] = fv.z; capv[4 * q + 3] = fv.w;
             }
@@ -976,8 +1039,35 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
         const u64 hp = __ldcg(&ctl->hub_pack[s3]);
         const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
         unsigned pos, j, nch;
-        if (nchunks)
-            while (grab_wchunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap);
+        if (nchunks) {
+            if (L == kBCSR && c.stage) {
+                // Staged: the warp takes its next chunk before working on the
+                // current one and copies the next chunk's entries into its
+                // other buffer meanwhile.
+                int *wb = c.stage + (threadIdx.x >> 5) * kStageInts;
+                bool have = grab_wchunk(c, s3, set, nh, nchunks, pos, j, nch);
+                bool st = have && stage_wchunk<L>(c, set, pos, j, wb);
+                cp_async_commit();
+                int b = 0;
+                while (have) {
+                    unsigned pos2, j2, nch2;
+                    const bool have2 = grab_wchunk(c, s3, set, nh, nchunks, pos2, j2, nch2);
+                    const bool st2 = have2 && stage_wchunk<L>(c, set, pos2, j2, wb + (b ^ 1) * 2 * kWChunk);
+                    cp_async_commit();
+                    cp_async_wait<1>();  // the current chunk's copies are done
+                    pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap, st ? wb + b * 2 * kWChunk : nullptr);
+                    pos = pos2;
+                    j = j2;
+                    nch = nch2;
+                    have = have2;
+                    st = st2;
+                    b ^= 1;
+                }
+                cp_async_wait<0>();
+            } else {
+                while (grab_wchunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap);
+            }
+        }
     }
     warp_clock_add(c, wt0);
 }
@@ -1990,7 +2080,9 @@ template <int L, int SW>
 __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) solve_kernel(Params P)
 {
     __shared__ Smem sm;
-    Ctx c{P, sm, 0ull, 0, gridDim.x, blockIdx.x, 0ull, 0ull, 0ull};
+    extern __shared__ __align__(16) int dyn_smem[];
+    Ctx c{P, sm, 0ull, 0, gridDim.x, blockIdx.x, 0ull, 0ull, 0ull,
+          dynamic_smem_bytes() >= (unsigned)kStageBytes ? dyn_smem : nullptr};
     solve_instance<L, SW>(c);
 }
 
@@ -2149,7 +2241,7 @@ __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) server_kernel(ServerD
                 if (threadIdx.x == 0) D.team_exit[team] = 5;
                 return;
             }
-            Ctx c{P, sm, 0ull, 0, tsize, rank, 0ull, 0ull, 0ull};
+            Ctx c{P, sm, 0ull, 0, tsize, rank, 0ull, 0ull, 0ull, nullptr};
             solve_instance<L, SW>(c);
         }
         if (rank == 0 && threadIdx.x == 0) {

@@ -35,6 +35,10 @@ constexpr int kChunk = 2048;        // hub rows of a BFS level or of the cut are
 #endif
 constexpr int kWChunk = WBPR_WCHUNK;  // hub rows of a push-relabel pass: chunks of this many entries,
                                       // one chunk per warp (kWChunk / 32 per lane), taken dynamically
+// Staging of push-relabel hub chunks in shared memory: per warp two buffers
+// of kWChunk entries (neighbour ids and residual capacities).
+constexpr int kStageInts = 2 * 2 * WBPR_WCHUNK;            // per warp
+constexpr int kStageBytes = (kBlock / 32) * kStageInts * 4;  // per block (dynamic shared memory)
 
 enum Layout : int { kRCSR = 0, kBCSR = 1 };
 
@@ -188,9 +192,9 @@ cudaError_t server_max_blocks_per_sm(int layout, int *blocks);
 cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream);
 
 // Launch helpers implemented in solver.cu.
-cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks);
+cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks, size_t dyn_smem = 0);
 cudaError_t solver_launch(int layout, int small_tile, int grid, const Params &p,
-                          cudaStream_t stream);
+                          cudaStream_t stream, size_t dyn_smem = 0);
 
 // Edge-flow kernels (solver.cu).
 cudaError_t launch_edge_flow(int layout, long long m, const unsigned *arc2slot,
