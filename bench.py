@@ -50,13 +50,13 @@ WORKLOADS = {
     "rmat20": dict(scale=20, seed=2, cap_hi=1000),
 }
 
-# The library's own kernels per step: the BCSR build (half_keys, tail_caps,
-# scatter_prefix, run_heads, merge_runs, pair_slots, max_degree_kernel; plus
-# count_degrees, iota_u32, invert_order, remap_arcs when the handle is
-# renumbered), solve_kernel for the flow and for the cut, and
-# edge_flow_kernel.  CUB's sort and scan kernels come on top.
+# The library's own kernels per step: the BCSR build (half_keys, sorted_caps,
+# scatter_prefix, run_heads, merge_runs, rev_slots, pair_slots,
+# max_degree_kernel; plus count_degrees_warp, iota_u32, invert_order,
+# remap_arcs when the handle is renumbered), solve_kernel for the flow and
+# for the cut, and edge_flow_kernel.  CUB's sort and scan kernels come on top.
 def launches_per_step(renumbered: bool) -> int:
-    return 10 + (4 if renumbered else 0)
+    return 11 + (4 if renumbered else 0)
 
 
 # Algorithmic bytes per unit of the BCSR solver (each unit is counted by the

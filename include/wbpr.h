@@ -124,7 +124,9 @@ typedef struct wbpr_options {
     int32_t stage_hubs;       /* 1 = stage the residual-list chunks of hub rows in shared
                                  memory: a warp copies its next chunk (cp.async) while
                                  it works on the current one (BCSR; 32 KB of shared
-                                 memory per block).  0 = read them directly. */
+                                 memory per block).  0 = read them directly (default:
+                                 the 4 x 49 KB of shared memory per SM leave the
+                                 global-relabel BFS too little L1). */
     int32_t barrier_extra;    /* for tests of the device wait limit only: every grid
                                  barrier waits for this many arrivals more than the
                                  grid has, so its wait runs out after
@@ -324,7 +326,7 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
  * that own no CUDA allocator.  It calls no cudaMalloc, cudaFree or allocating
  * library routine: the solver's working set (residual capacities, excesses,
  * heights, queues, control block) lives in one fixed device array of about
- * 15 MiB that every GPU loading the library holds until the process exits.
+ * 15.6 MiB that every GPU loading the library holds until the process exits.
  *   n, slots   vertex count (2 .. WBPR_NOALLOC_MAX_VERTICES) and BCSR entry
  *              count (0 .. WBPR_NOALLOC_MAX_SLOTS); larger graphs are rejected
  *              with WBPR_EINVAL.

@@ -103,7 +103,7 @@ void wbpr_default_options(wbpr_options *o)
     o->renumber = -1;
     o->thread_centric = 0;
     o->warp_time = 0;
-    o->stage_hubs = 1;
+    o->stage_hubs = 0;
     o->barrier_extra = 0;
 }
 

@@ -78,12 +78,17 @@ static void *pick_kernel(int layout, int small_tile)
     return solve_kernel_rcsr_8();
 }
 
-// A launch with the hub-chunk stage needs 4 x (static + 32 KB) of shared
-// memory per SM: ask for a carveout that holds it (else the default split).
+// A launch with the hub-chunk stage uses 16.8 KB of static and 32 KB of
+// dynamic shared memory per block: more than the 48 KB a kernel gets without
+// opting in, so the kernel opts in to that much dynamic shared memory, and
+// asks for the largest shared-memory carveout so that four such blocks fit
+// on an SM (a cooperative launch is sized from this occupancy).
 static cudaError_t set_carveout(void *kernel, size_t dyn_smem)
 {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                dyn_smem ? 90 : (int)cudaSharedmemCarveoutDefault);
+                                dyn_smem ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault);
 }
 
 cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks, size_t dyn_smem)
