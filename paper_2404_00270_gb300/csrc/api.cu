@@ -410,6 +410,7 @@ Params make_params(wbpr_graph *g, int mode)
     p.g.s = g->s_int;
     p.g.t = g->t_int;
     p.g.order = g->order;
+    p.g.perm = g->perm;
     p.g.slots = g->slots;
     p.g.off = g->off;
     p.g.col = g->col;

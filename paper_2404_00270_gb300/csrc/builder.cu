@@ -88,13 +88,17 @@ __global__ void half_keys(long long m, int n, int b, u64 loop_key, const int *sr
 // Capacity of each sorted half-entry's arc, in sorted order: c on its tail
 // side, -(c + 1) on its head side (c >= 0), so that later passes read both
 // sums of a run sequentially instead of gathering cap[] again.
-__global__ void sorted_caps(long long len, const unsigned *pos, const int *cap, int *out)
+// Also flags (dup = 1) a parallel arc: two tail-side half-entries with the
+// same key, the only case that needs the duplicate prefix.
+__global__ void sorted_caps(long long len, const u64 *key, const unsigned *pos, const int *cap, int *out,
+                            int *dup)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
         const unsigned p = pos[j];
         const int c = cap[p >> 1];
         out[j] = (p & 1u) ? -c - 1 : c;
+        if (j > 0 && (p & 1u) == 0 && key[j] == key[j - 1] && (pos[j - 1] & 1u) == 0) *dup = 1;
     }
 }
 
@@ -424,6 +428,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
     g->s_int = g->s;
     g->t_int = g->t;
     g->order = nullptr;
+    g->perm = nullptr;
     if (g->renumbered && m > 0) {
         unsigned *deg, *degs, *ids;
         BUILD_ALLOC(deg, unsigned, n, pool);
@@ -450,7 +455,8 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         pool.release(degs);
         pool.release(deg);
         int *perm, *rsrc, *rdst;
-        BUILD_ALLOC(perm, int, n, pool);
+        OWN_ALLOC(g->perm, int, n);
+        perm = g->perm;
         BUILD_ALLOC(rsrc, int, m, pool);
         BUILD_ALLOC(rdst, int, m, pool);
         invert_order<<<grid_for(n), 256, 0, st>>>(n, g->order, perm);
@@ -460,7 +466,6 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_CUDA(cudaMemcpyAsync(&st_int[0], perm + g->s, sizeof(int), cudaMemcpyDeviceToHost, st));
         BUILD_CUDA(cudaMemcpyAsync(&st_int[1], perm + g->t, sizeof(int), cudaMemcpyDeviceToHost, st));
         BUILD_CUDA(cudaStreamSynchronize(st));
-        pool.release(perm);
         g->s_int = st_int[0];
         g->t_int = st_int[1];
         src = rsrc;
@@ -526,24 +531,11 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         if (m > 0) BUILD_CUDA(cudaMemcpyAsync(g->cap_in, cap, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st));
         BUILD_CUDA(cudaMemsetAsync(g->prefix, 0, sizeof(int) * (size_t)(m > 0 ? m : 1), st));
         int *cj = nullptr;
+        int *dup = bad + 2;   // zeroed with the other flags
         if (len > 0) {
-            int *pre;
             BUILD_ALLOC(cj, int, len, pool);
-            BUILD_ALLOC(pre, int, len, pool);
-            sorted_caps<<<grid_for(len), 256, 0, st>>>(len, v2s, cap, cj);
+            sorted_caps<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, cap, cj, dup);
             BUILD_CUDA(cudaGetLastError());
-            auto tails = thrust::make_transform_iterator(cj, TailPart());
-            size_t nb = 0;
-            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, k2s, tails, pre, (int64_t)len,
-                                                          cuda::std::equal_to<>(), st));
-            void *t2 = pool.get(nb);
-            if (!t2) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, k2s, tails, pre, (int64_t)len,
-                                                          cuda::std::equal_to<>(), st));
-            pool.release(t2);
-            scatter_prefix<<<grid_for(len), 256, 0, st>>>(len, v2s, pre, g->prefix);
-            BUILD_CUDA(cudaGetLastError());
-            pool.release(pre);
         }
 
         // ---- merge runs into slots ------------------------------------------------
@@ -560,7 +552,26 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             BUILD_CUDA(cub::DeviceScan::InclusiveSum(t4, nb, heads, heads, (int64_t)len, st));
             pool.release(t4);
             BUILD_CUDA(cudaMemcpyAsync(&S, heads + (len - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            int h_dup = 0;
+            BUILD_CUDA(cudaMemcpyAsync(&h_dup, dup, sizeof(int), cudaMemcpyDeviceToHost, st));
             BUILD_CUDA(cudaStreamSynchronize(st));
+            if (h_dup) {
+                // parallel arcs: each one's prefix (capacity of its earlier duplicates)
+                int *pre;
+                BUILD_ALLOC(pre, int, len, pool);
+                auto tails = thrust::make_transform_iterator(cj, TailPart());
+                size_t nb = 0;
+                BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(nullptr, nb, k2s, tails, pre, (int64_t)len,
+                                                              cuda::std::equal_to<>(), st));
+                void *t2 = pool.get(nb);
+                if (!t2) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+                BUILD_CUDA(cub::DeviceScan::ExclusiveSumByKey(t2, nb, k2s, tails, pre, (int64_t)len,
+                                                              cuda::std::equal_to<>(), st));
+                pool.release(t2);
+                scatter_prefix<<<grid_for(len), 256, 0, st>>>(len, v2s, pre, g->prefix);
+                BUILD_CUDA(cudaGetLastError());
+                pool.release(pre);
+            }
         }
         g->slots = S;
         unsigned *slot_by_pos;

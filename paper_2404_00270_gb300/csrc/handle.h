@@ -47,6 +47,7 @@ struct wbpr_graph {
 
     // graph (device)
     int *order = nullptr;     // renumbered: solver id -> input id
+    int *perm = nullptr;      // renumbered: input id -> solver id
     long long *off = nullptr;
     int *col = nullptr;
     int *cf = nullptr;

@@ -266,6 +266,7 @@ __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
         int z = (gen + 2) % 3;
         for (int k = 0; k < kClasses; ++k) ctl->q_count[z][k] = 0;
         ctl->q_grab[z] = 0;
+        ctl->q_grab_w[z] = 0;
         ctl->hub_pack[z] = 0;
         ctl->gap_level[z] = kUnvisited;
     }
@@ -789,24 +790,56 @@ __device__ void mp_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
 }
 
 // Take the next hub chunk of generation (s3, set): warp-uniform result.
-__device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks,
+// Chunk ids are reserved in batches (one atomic on the generation's counter
+// per `WGrab::batch` chunks), so that hundreds of thousands of chunks per
+// pass do not all meet on one counter.
+struct WGrab {
+    unsigned next, end, batch;
+    __device__ WGrab(unsigned nchunks, unsigned nwarps) : next(0), end(0), batch(nchunks / (8u * nwarps) + 1u) {}
+};
+
+__device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks, WGrab &gb,
                                             unsigned &pos, unsigned &j, unsigned &nch)
 {
-    unsigned id = 0, lo = 0, s0 = 0, s1 = 0;
+    if (gb.next >= gb.end) {
+        unsigned b = 0;
+        if ((threadIdx.x & 31) == 0) b = atomicAdd(&c.P.st.ctl->q_grab[s3], gb.batch);
+        b = __shfl_sync(kFull, b, 0);
+        gb.next = b;
+        gb.end = b + gb.batch < nchunks ? b + gb.batch : nchunks;
+    }
+    if (gb.next >= nchunks) return false;
+    const unsigned id = gb.next++;
+    unsigned lo = 0, s0 = 0, s1 = 0;
     if ((threadIdx.x & 31) == 0) {
-        id = atomicAdd(&c.P.st.ctl->q_grab[s3], 1u);
-        if (id < nchunks) {
+        {
             const unsigned *start = c.P.st.hub_start[set];
             lo = __ldcg(c.P.st.hub_chunk[set] + id);  // start[lo] <= id < start[lo + 1]
             s0 = __ldcg(start + lo);
             s1 = lo + 1 < nh ? __ldcg(start + lo + 1) : nchunks;
         }
     }
-    id = __shfl_sync(kFull, id, 0);
     pos = __shfl_sync(kFull, lo, 0);
     j = id - __shfl_sync(kFull, s0, 0);
     nch = __shfl_sync(kFull, s1, 0) - __shfl_sync(kFull, s0, 0);
-    return id < nchunks;
+    return true;
+}
+
+// Rows of the warp class, taken dynamically by warps in batches of `batch`
+// (one atomic per batch): the next row index for the calling warp, or
+// `count` when none is left.  Warp-uniform.
+__device__ __forceinline__ unsigned grab_rows(unsigned *ctr, unsigned count, unsigned batch, unsigned &next,
+                                              unsigned &end)
+{
+    if (next >= end) {
+        unsigned b = 0;
+        if ((threadIdx.x & 31) == 0) b = atomicAdd(ctr, batch);
+        b = __shfl_sync(kFull, b, 0);
+        next = b;
+        end = b + batch < count ? b + batch : count;
+        if (b >= count) return count;
+    }
+    return next++;
 }
 
 // Starts the copies of this lane's 8 entries of hub chunk (pos, j) into the
@@ -1013,8 +1046,14 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
     const unsigned gwarp = c.bid * kWarps + (threadIdx.x >> 5);
     const unsigned nwarps = c.nblk * kWarps;
     {
+        // warp-class rows: taken dynamically, in batches (their lengths vary
+        // from small_max to warp_max entries)
         const int *q1 = P.st.q[set][1];
-        for (unsigned i = gwarp; i < c1; i += nwarps) {
+        const unsigned batch = c1 / (8u * nwarps) + 1u;
+        unsigned next = 0, end = 0;
+        for (;;) {
+            const unsigned i = grab_rows(&ctl->q_grab_w[s3], c1, batch, next, end);
+            if (i >= c1) break;
             if (P.multi_push) mp_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
             else pr_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
         }
@@ -1045,13 +1084,14 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
                 // current one and copies the next chunk's entries into its
                 // other buffer meanwhile.
                 int *wb = c.stage + (threadIdx.x >> 5) * kStageInts;
-                bool have = grab_wchunk(c, s3, set, nh, nchunks, pos, j, nch);
+                WGrab gb(nchunks, c.nblk * kWarps);
+                bool have = grab_wchunk(c, s3, set, nh, nchunks, gb, pos, j, nch);
                 bool st = have && stage_wchunk<L>(c, set, pos, j, wb);
                 cp_async_commit();
                 int b = 0;
                 while (have) {
                     unsigned pos2, j2, nch2;
-                    const bool have2 = grab_wchunk(c, s3, set, nh, nchunks, pos2, j2, nch2);
+                    const bool have2 = grab_wchunk(c, s3, set, nh, nchunks, gb, pos2, j2, nch2);
                     const bool st2 = have2 && stage_wchunk<L>(c, set, pos2, j2, wb + (b ^ 1) * 2 * kWChunk);
                     cp_async_commit();
                     cp_async_wait<1>();  // the current chunk's copies are done
@@ -1065,7 +1105,8 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
                 }
                 cp_async_wait<0>();
             } else {
-                while (grab_wchunk(c, s3, set, nh, nchunks, pos, j, nch)) pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap);
+                WGrab gb(nchunks, c.nblk * kWarps);
+                while (grab_wchunk(c, s3, set, nh, nchunks, gb, pos, j, nch)) pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap);
             }
         }
     }
@@ -1273,7 +1314,7 @@ __device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int 
     if (fresh) {
         const long long d = degree<L>(P.g, v);
         const int cls = classify(P, d);
-        if (cls == 2) hub_append(c, n3, nset, v, d, false, 0);
+        if (cls == 2) hub_append(c, n3, nset, v, d, false, 0, kWChunk, hub_lead<L>(P.g, v));
         else q_append(c, n3, nset, cls, v);
     }
 }
@@ -1356,12 +1397,17 @@ __device__ void bfs_row(Ctx &c, int w, int sl, int val, int nset, int n3)
     }
 }
 
-// Scan one chunk of frontier hub w with the whole block.
+// Scan one chunk of kWChunk entries of frontier hub w with one warp (the
+// chunk starts `lead` slots before the row, as in the push-relabel pass);
+// lane l takes entries l, l + 32, ... so that every load is coalesced, and
+// all loads of a stage are issued together.  Returns the row entries of the
+// chunk on lane 0 (0 elsewhere).
 template <int L, int DIR>
-__device__ long long bfs_chunk(Ctx &c, int set, unsigned pos, unsigned j, int val, int nset, int n3)
+__device__ long long bfs_wchunk(Ctx &c, int set, unsigned pos, unsigned j, int val, int nset, int n3)
 {
-    constexpr int NB = kChunk / kBlock;
+    constexpr int NB = kWChunk / 32;
     const GraphDev &g = c.P.g;
+    const int lane = threadIdx.x & 31;
     const int w = __ldcg(c.P.st.q[set][2] + pos);
     const long long ob = __ldg(g.off + w), dout = __ldg(g.off + w + 1) - ob;
     long long ib = 0, din = 0;
@@ -1370,19 +1416,20 @@ __device__ long long bfs_chunk(Ctx &c, int set, unsigned pos, unsigned j, int va
         din = __ldg(g.in_off + w + 1) - ib;
     }
     const long long deg = dout + din;
-    const long long r0 = (long long)j * kChunk;
-    const long long r1 = deg < r0 + kChunk ? deg : r0 + kChunk;
+    const long long lo = (long long)j * kWChunk - (L == kBCSR ? (ob & 3) : 0);
     long long k[NB];
     bool in[NB], ok[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-        const long long r = r0 + threadIdx.x + (long long)q * kBlock;
-        ok[q] = r < r1;
+        const long long r = lo + lane + 32LL * q;
+        ok[q] = r >= 0 && r < deg;
         k[q] = row_slot<L>(ob, dout, ib, ok[q] ? r : 0, in[q]);
     }
     bfs_entries<L, DIR, NB>(c, w, k, in, ok, val, nset, n3);
-    return r1 > r0 ? r1 - r0 : 0;
+    const long long hi = lo + kWChunk < deg ? lo + kWChunk : deg;
+    return lane == 0 && hi > (lo > 0 ? lo : 0) ? hi - (lo > 0 ? lo : 0) : 0;
 }
+
 
 // Consume frontier generation `gen`, produce generation gen + 1.
 template <int L, int DIR, int SW>
@@ -1396,27 +1443,18 @@ __device__ void bfs_level(Ctx &c, int val)
     const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
     long long scanned = 0;
-    {
-        const u64 hp = __ldcg(&ctl->hub_pack[s3]);
-        const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
-        unsigned pos, j, nch;
-        if (nchunks) {
-            while (grab_chunk(c, s3, set, nh, nchunks, pos, j, nch)) {
-                const long long k = bfs_chunk<L, DIR>(c, set, pos, j, val, nset, n3);
-                if (threadIdx.x == 0) scanned += k;
-                __syncthreads();
-                unsigned mx = c.sm.qcnt[0] > c.sm.qcnt[1] ? c.sm.qcnt[0] : c.sm.qcnt[1];
-                if (mx > (unsigned)(kQueueCap / 2)) q_flush(c, n3, nset);
-            }
-        }
-    }
     const int lane = threadIdx.x & 31;
-    const unsigned gwarp = c.bid * kWarps + (threadIdx.x >> 5);
     const unsigned nwarps = c.nblk * kWarps;
     {
+        // warp-class rows (up to warp_max entries, of uneven length): taken
+        // dynamically, in batches that keep the atomics few
         const int *q1 = P.st.q[set][1];
-        for (unsigned i = gwarp; i < c1; i += nwarps) {
-            int w = __ldcg(q1 + i);
+        const unsigned batch = c1 / (8u * nwarps) + 1u;
+        unsigned next = 0, end = 0;
+        for (;;) {
+            const unsigned i = grab_rows(&ctl->q_grab_w[s3], c1, batch, next, end);
+            if (i >= c1) break;
+            const int w = __ldcg(q1 + i);
             bfs_row<L, DIR, 32>(c, w, lane, val, nset, n3);
             if (lane == 0) scanned += degree<L>(P.g, w);
         }
@@ -1430,6 +1468,17 @@ __device__ void bfs_level(Ctx &c, int val)
             int w = __ldcg(q0 + i);
             bfs_row<L, DIR, SW>(c, w, sl, val, nset, n3);
             if (sl == 0) scanned += degree<L>(P.g, w);
+        }
+    }
+    {
+        // hub rows last: 256-entry chunks taken dynamically, one warp each
+        const u64 hp = __ldcg(&ctl->hub_pack[s3]);
+        const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
+        unsigned pos, j, nch;
+        if (nchunks) {
+            WGrab gb(nchunks, nwarps);
+            while (grab_wchunk(c, s3, set, nh, nchunks, gb, pos, j, nch))
+                scanned += bfs_wchunk<L, DIR>(c, set, pos, j, val, nset, n3);
         }
     }
     q_flush(c, n3, nset);
@@ -1493,7 +1542,7 @@ __device__ __forceinline__ void bu_found(Ctx &c, int v, long long deg, int val, 
 {
     __stcg(bfs_levels<DIR>(c.P) + v, val);
     const int cls = classify(c.P, deg);
-    if (cls == 2) hub_append(c, n3, nset, v, deg, false, 0);
+    if (cls == 2) hub_append(c, n3, nset, v, deg, false, 0, kWChunk, hub_lead<L>(c.P.g, v));
     else q_append(c, n3, nset, cls, v);
 }
 
@@ -1759,7 +1808,7 @@ __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
         const int cls = classify(c.P, d);
         c.P.st.q[gen & 1][cls][0] = v;
         if (cls == 2) {
-            const unsigned nch = hub_chunks(d);
+            const unsigned nch = hub_chunks(d, kWChunk, hub_lead<L>(c.P.g, v));
             c.P.st.hub_start[gen & 1][0] = 0;
             for (unsigned j = 0; j < nch; ++j) c.P.st.hub_chunk[gen & 1][j] = 0;
             c.P.st.ctl->hub_pack[gen % 3] = (1ull << 40) | nch;
@@ -2033,9 +2082,11 @@ __device__ bool min_cut(Ctx &c)
     if (!cut_capacity<L>(c, sum)) return false;
     long long bs = block_sum(c, sum);
     if (threadIdx.x == 0 && bs) atomicAdd((u64 *)&P.st.ctl->cut_value, (u64)bs);
+    // the cut side in input ids: a renumbered handle gathers through the
+    // inverse order, so that the byte writes stay coalesced
     if (P.source_side)
-        for (long long v = tid; v < n; v += stride)
-            P.source_side[g.order ? __ldg(g.order + v) : v] = (unsigned char)(__ldcg(mark + v) != 0);
+        for (long long i = tid; i < n; i += stride)
+            P.source_side[i] = (unsigned char)(__ldcg(mark + (g.perm ? __ldg(g.perm + i) : i)) != 0);
     return grid_sync(c, 32);
 }
 

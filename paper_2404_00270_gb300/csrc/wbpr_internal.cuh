@@ -70,6 +70,7 @@ struct __align__(128) Ctl {
     long long cut_value;
     unsigned q_count[3][kClasses];  // queue sizes by generation % 3 and class (0, 1)
     unsigned q_grab[3];             // dynamic work counter of the hub chunks
+    unsigned q_grab_w[3];           // dynamic work counter of the warp-class rows
     unsigned long long hub_pack[3]; // hub class: (count << 40) | total chunks
     int done;
     unsigned trace_len;
@@ -94,7 +95,8 @@ struct GraphDev {
     const long long *in_off;    // RCSR
     const int *in_col;          // RCSR
     const unsigned *flow_idx;   // RCSR
-    const int *order;           // renumbered handle: solver id -> input id (cut side output); or null
+    const int *order;           // renumbered handle: solver id -> input id; or null
+    const int *perm;            // renumbered handle: input id -> solver id (cut side output); or null
 };
 
 // Upper bound on the hub chunks of one queue generation: a hub of degree d

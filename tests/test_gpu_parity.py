@@ -354,3 +354,21 @@ def test_autotune_keeps_the_value():
     for k, v in cfg.items():
         setattr(o, k, v)
     check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
+
+
+@pytest.mark.parametrize("warp_max", [16, 1024])
+def test_staged_hub_chunks_same_results(warp_max):
+    """Hub rows read through the shared-memory stage (stage_hubs = 1), with
+    many hubs (rows over 16 entries) or the default class bounds."""
+    m = wb()
+    o = m.wbpr_default_options()
+    o.stage_hubs = 1
+    o.warp_max_degree = warp_max
+    o.small_max_degree = min(8, warp_max)
+    for g in (W.rmat(14, 16, 2), W.bipartite_zipf(4096, 4096, 3), W.grid(40, 40, 47), W.rmat(12, 16, 45)):
+        src, dst, cap = g.numpy()
+        check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
+    o.renumber = 1
+    g = W.rmat(14, 16, 41)
+    src, dst, cap = g.numpy()
+    check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
