@@ -47,6 +47,7 @@ sys.path.insert(0, ROOT)
 UNIT = "arcs/s"
 WORKLOADS = {
     "rmat26": dict(scale=26, seed=4, cap_hi=10000),
+    "rmat22": dict(scale=22, seed=2, cap_hi=1000),   # a small case of the same kernel, for profiling
     "rmat20": dict(scale=20, seed=2, cap_hi=1000),
 }
 
@@ -382,6 +383,12 @@ def run_gpu(args):
         hcap = g.cap.cpu().pin_memory()
         hflow = torch.empty(m, dtype=torch.int32).pin_memory()
         hside = torch.empty(n, dtype=torch.uint8).pin_memory()
+        # one untimed step first: the library's staging buffers for host
+        # inputs and outputs come from the caching allocator on first use
+        G = wb.wbpr_build(n, m, hsrc, hdst, hcap, s, t, wb.WBPR_BCSR, None, stream)
+        wb.wbpr_maxflow(G, stream, hflow)
+        wb.wbpr_mincut(G, stream, hside)
+        G.close()
         barrier()
         t0 = time.perf_counter()
         e_arcs = 0
@@ -658,7 +665,7 @@ def main():
     ap.add_argument("--impl", default="wbpr", choices=["wbpr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
-    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "rmat20", "batch", "ablation"])
+    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "rmat22", "rmat20", "batch", "ablation"])
     ap.add_argument("--batch-block", type=int, default=256,
                     help="instances of the batch / serving block in config (0 = none)")
     ap.add_argument("--batch-count", type=int, default=1024)

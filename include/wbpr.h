@@ -90,7 +90,7 @@ typedef struct wbpr_options {
                                  queue sizes); read with wbpr_export(WBPR_ARRAY_TRACE) */
     float gr_ratio;           /* > 0: start a global relabel once the push-relabel
                                  iterations since the last one took gr_ratio times
-                                 as long as it did (default 1.0); `cycle` then only
+                                 as long as it did (default 1.5); `cycle` then only
                                  caps the iterations in between.  0 = every `cycle`
                                  iterations */
     int32_t batch_team;       /* wbpr_maxflow_batch: blocks that solve one large

@@ -95,7 +95,7 @@ void wbpr_default_options(wbpr_options *o)
     o->barrier_timeout_ms = 20000;
     o->max_iterations = (int64_t)1 << 40;
     o->trace = 0;
-    o->gr_ratio = 1.0f;
+    o->gr_ratio = 1.5f;
     o->batch_team = 16;
     o->batch_big_slots = (int64_t)1 << 15;
     o->bottom_up = 14;
