@@ -99,12 +99,14 @@ typedef struct wbpr_options {
                                  slots than this are large (default 2^15); smaller
                                  ones are solved by a single block each */
     int32_t bottom_up;        /* BFS direction (global relabel and min cut).  A level whose
-                                 frontier F satisfies |F| * bottom_up >= (vertices
-                                 not yet visited) and |F| >= bottom_up_min runs
-                                 bottom-up: every unvisited vertex looks for a
-                                 residual arc into F and stops at the first.
-                                 Otherwise top-down.  0 = always top-down.
-                                 Default 14 */
+                                 frontier F has at least bottom_up_min vertices and
+                                 whose residual-list entries times bottom_up reach
+                                 those of the vertices not yet visited (or, with
+                                 bottom_up_edges = 0, |F| * bottom_up >= the
+                                 vertices not yet visited) runs bottom-up: every
+                                 unvisited vertex looks for a residual arc into F
+                                 and stops at the first.  Otherwise top-down.
+                                 0 = always top-down.  Default 14 */
     int32_t bottom_up_min;    /* default 1024 */
     int32_t renumber;         /* vertex numbering of the solver, fixed at build time:
                                  1 = renumber by endpoint count, largest first
@@ -133,6 +135,10 @@ typedef struct wbpr_options {
                                  barrier_timeout_ms and the solve returns
                                  WBPR_ETIMEOUT (0..1024, default 0; grids of one
                                  block do not wait) */
+    int32_t bottom_up_edges;  /* BFS direction rule: 1 = compare the residual-list
+                                 entries of the frontier, times bottom_up, with
+                                 those of the vertices not yet visited; 0 = compare
+                                 vertex counts (default) */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */

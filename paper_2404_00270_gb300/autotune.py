@@ -25,6 +25,7 @@ from . import (Options, WBPR_BCSR, wbpr_build, wbpr_default_options, wbpr_get_in
                wbpr_get_stats, wbpr_maxflow, wbpr_set_options)
 
 KNOBS = ("small_tile", "small_max_degree", "warp_max_degree", "grid_blocks", "gr_ratio", "bottom_up")
+# bottom_up_edges (the form of the direction rule) is left at its default.
 
 
 def graph_class(n: int, slots: int, max_degree: int) -> str:

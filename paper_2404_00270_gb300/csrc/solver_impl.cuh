@@ -119,6 +119,7 @@ struct Ctx {
     unsigned bid;
     u64 gr_start_ns, gr_ns, gr_end_ns;  // last global relabel (rank 0, thread 0)
     int *stage;      // dynamic shared memory for staging hub chunks (kStageBytes), or null
+    long long fe;    // this thread's share of the next frontier's residual-list entries
 };
 
 // Asynchronous 16-byte copies global -> shared (cp.async, L2 only), and the
@@ -267,6 +268,7 @@ __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
         for (int k = 0; k < kClasses; ++k) ctl->q_count[z][k] = 0;
         ctl->q_grab[z] = 0;
         ctl->q_grab_w[z] = 0;
+        ctl->fedges[z] = 0;
         ctl->hub_pack[z] = 0;
         ctl->gap_level[z] = kUnvisited;
     }
@@ -1313,6 +1315,7 @@ __device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int 
     }
     if (fresh) {
         const long long d = degree<L>(P.g, v);
+        c.fe += d;
         const int cls = classify(P, d);
         if (cls == 2) hub_append(c, n3, nset, v, d, false, 0, kWChunk, hub_lead<L>(P.g, v));
         else q_append(c, n3, nset, cls, v);
@@ -1483,6 +1486,9 @@ __device__ void bfs_level(Ctx &c, int val)
     }
     q_flush(c, n3, nset);
     if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
+    const long long bfe = block_sum(c, c.fe);   // the next frontier's entries, for the direction rule
+    if (threadIdx.x == 0 && bfe) atomicAdd((u64 *)&P.st.ctl->fedges[n3], (u64)bfe);
+    c.fe = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1541,6 +1547,7 @@ template <int L, int DIR>
 __device__ __forceinline__ void bu_found(Ctx &c, int v, long long deg, int val, int nset, int n3)
 {
     __stcg(bfs_levels<DIR>(c.P) + v, val);
+    c.fe += deg;
     const int cls = classify(c.P, deg);
     if (cls == 2) hub_append(c, n3, nset, v, deg, false, 0, kWChunk, hub_lead<L>(c.P.g, v));
     else q_append(c, n3, nset, cls, v);
@@ -1688,6 +1695,9 @@ __device__ void bfs_level_bu(Ctx &c, int val)
     }
     q_flush(c, n3, nset);
     if (scanned) atomicAdd((unsigned long long *)&c.sm.stats[kStatGrArcs], (u64)scanned);
+    const long long bfe = block_sum(c, c.fe);   // the next frontier's entries, for the direction rule
+    if (threadIdx.x == 0 && bfe) atomicAdd((u64 *)&P.st.ctl->fedges[n3], (u64)bfe);
+    c.fe = 0;
 }
 
 // Capacity of the out-arcs from the marked side (mark != 0) to the rest,
@@ -1799,6 +1809,19 @@ __device__ bool cut_capacity(Ctx &c, long long &sum)
     return true;
 }
 
+// Direction of the next BFS level (after Beamer, Asanovic and Patterson):
+// bottom-up when the frontier holds at least bottom_up_min vertices and,
+// with bottom_up_edges, its residual-list entries times bottom_up reach the
+// entries of the vertices not yet visited (nor written off); otherwise its
+// vertex count times bottom_up must reach the unvisited vertices.
+__device__ __forceinline__ bool bottom_up_level(const Params &P, unsigned tot, long long fe, long long unseen_edges,
+                                                long long unseen)
+{
+    if (P.bottom_up <= 0 || tot < (unsigned)P.bottom_up_min) return false;
+    if (P.bottom_up_edges) return fe * P.bottom_up >= unseen_edges;
+    return (long long)tot * P.bottom_up >= unseen;
+}
+
 // Seed a BFS: generation `gen` holds the single vertex v.
 template <int L>
 __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
@@ -1807,6 +1830,7 @@ __device__ __forceinline__ void seed_queue(Ctx &c, int gen, int v)
         const long long d = degree<L>(c.P.g, v);
         const int cls = classify(c.P, d);
         c.P.st.q[gen & 1][cls][0] = v;
+        c.P.st.ctl->fedges[gen % 3] = d;
         if (cls == 2) {
             const unsigned nch = hub_chunks(d, kWChunk, hub_lead<L>(c.P.g, v));
             c.P.st.hub_start[gen & 1][0] = 0;
@@ -1837,7 +1861,10 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
     const bool gap = phase1 && P.gap;
     if (c.bid == 0 && threadIdx.x == 0) {
         c.gr_start_ns = global_ns();
-        if (first_of_phase2) P.st.ctl->dead_count = 0;  // the marks are cleared below
+        if (first_of_phase2) {  // the marks are cleared below
+            P.st.ctl->dead_count = 0;
+            P.st.ctl->dead_edges = 0;
+        }
     }
     const long long stride = (long long)c.nblk * kBlock;
     for (long long v = c.bid * kBlock + threadIdx.x; v <= n; v += stride) {
@@ -1859,13 +1886,15 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
     // to the target can appear for them, because no push ever enters a
     // vertex at the height cap.
     long long seen = __ldcg(&P.st.ctl->dead_count);
+    long long unseen_edges = (L == kRCSR ? 2 : 1) * g.slots - __ldcg(&P.st.ctl->dead_edges);
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
         if (gap && c.bid == 0 && threadIdx.x == 0 && level < n) __stcg(P.st.count + level, (int)tot);
         seen += tot;
-        const bool bu_mode = P.bottom_up > 0 && tot >= (unsigned)P.bottom_up_min &&
-                             (long long)tot * P.bottom_up >= (long long)n - seen;
+        const long long fe = __ldcg(&P.st.ctl->fedges[c.gen % 3]);
+        unseen_edges -= fe;
+        const bool bu_mode = bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen);
         if (bu_mode)
             bfs_level_bu<L, kBfsBackward>(c, base + level + 1);
         else
@@ -1873,7 +1902,7 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         if (!grid_sync(c, 11)) return false;
         c.gen++;
     }
-    long long wo = 0, nd = 0;
+    long long wo = 0, nd = 0, nde = 0;
     for (long long v = c.bid * kBlock + threadIdx.x; v < n; v += stride) {
         if (v == excluded) continue;
         if (__ldcg(P.st.h + v) == kUnvisited) {
@@ -1881,6 +1910,7 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
             if (!P.st.dead[v]) {
                 P.st.dead[v] = 1;
                 ++nd;
+                nde += degree<L>(g, (int)v);
                 if (phase1) wo += __ldcg(P.st.e + v);
             }
         }
@@ -1892,6 +1922,8 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
     }
     const long long bd = block_sum(c, nd);
     if (threadIdx.x == 0 && bd) atomicAdd((u64 *)&P.st.ctl->dead_count, (u64)bd);
+    const long long bde = block_sum(c, nde);
+    if (threadIdx.x == 0 && bde) atomicAdd((u64 *)&P.st.ctl->dead_edges, (u64)bde);
     if (c.bid == 0 && threadIdx.x == 0) P.st.ctl->global_relabels++;
     const bool ok = grid_sync(c, 12);
     if (c.bid == 0 && threadIdx.x == 0) {
@@ -2065,13 +2097,15 @@ __device__ bool min_cut(Ctx &c)
     // Forward BFS from s, bottom-up on large frontiers (the forward residual
     // w -> v of an entry of v's row: the mirror cfb in BCSR, else a lookup of
     // the reverse slot).
-    const bool bu_ok = P.bottom_up > 0;
     long long seen = 0;
+    long long unseen_edges = (L == kRCSR ? 2 : 1) * g.slots;
     for (int level = 0;; ++level) {
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) break;
         seen += tot;
-        if (bu_ok && tot >= (unsigned)P.bottom_up_min && (long long)tot * P.bottom_up >= (long long)n - seen)
+        const long long fe = __ldcg(&P.st.ctl->fedges[c.gen % 3]);
+        unseen_edges -= fe;
+        if (bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen))
             bfs_level_bu<L, kBfsForward>(c, level + 2);
         else
             bfs_level<L, kBfsForward, SW>(c, level + 2);
@@ -2133,7 +2167,7 @@ __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) solve_kernel(Params P
     __shared__ Smem sm;
     extern __shared__ __align__(16) int dyn_smem[];
     Ctx c{P, sm, 0ull, 0, gridDim.x, blockIdx.x, 0ull, 0ull, 0ull,
-          dynamic_smem_bytes() >= (unsigned)kStageBytes ? dyn_smem : nullptr};
+          dynamic_smem_bytes() >= (unsigned)kStageBytes ? dyn_smem : nullptr, 0};
     solve_instance<L, SW>(c);
 }
 
@@ -2292,7 +2326,7 @@ __global__ void __launch_bounds__(kBlock, WBPR_MIN_BLOCKS) server_kernel(ServerD
                 if (threadIdx.x == 0) D.team_exit[team] = 5;
                 return;
             }
-            Ctx c{P, sm, 0ull, 0, tsize, rank, 0ull, 0ull, 0ull, nullptr};
+            Ctx c{P, sm, 0ull, 0, tsize, rank, 0ull, 0ull, 0ull, nullptr, 0};
             solve_instance<L, SW>(c);
         }
         if (rank == 0 && threadIdx.x == 0) {

@@ -78,6 +78,8 @@ struct __align__(128) Ctl {
                          // global relabel due (-1 = none)
     int pad2;
     long long dead_count;    // vertices marked unreachable (dead[]) in the current phase
+    long long dead_edges;    // their residual-list entries
+    long long fedges[3];     // residual-list entries of the BFS frontier, by generation % 3
 };
 
 struct GraphDev {
@@ -152,6 +154,7 @@ struct Params {
     int bottom_up;               // > 0: bottom-up BFS levels when frontier * bottom_up >=
                                  //      unvisited vertices
     int bottom_up_min;           //      and frontier >= bottom_up_min
+    int bottom_up_edges;         // 1: compare the frontier's entries, not its vertices
     long long max_iterations;
     unsigned long long timeout_ns;
     unsigned char *source_side;  // kModeCut output (device, n bytes) or null

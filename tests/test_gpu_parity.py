@@ -147,12 +147,14 @@ def test_builder_arrays_bit_exact(layout):
         G.close()
 
 
-BU_MODES = {"top-down": (0, 1024), "default": (14, 1024), "bottom-up": (1 << 20, 1)}
+# (bottom_up, bottom_up_min, bottom_up_edges)
+BU_MODES = {"top-down": (0, 1024, 1), "default": (14, 1024, 1), "vertex-rule": (14, 1024, 0),
+            "bottom-up": (1 << 20, 1, 0)}
 
 
 def _bu_options(m, mode):
     o = m.wbpr_default_options()
-    o.bottom_up, o.bottom_up_min = BU_MODES[mode]
+    o.bottom_up, o.bottom_up_min, o.bottom_up_edges = BU_MODES[mode]
     return o
 
 

@@ -116,12 +116,12 @@ def test_paper_mode_bcsr_holds_no_reverse_index():
         G0.close()
 
 
-@pytest.mark.parametrize("bu", [(0, 1024), (14, 1024), (1 << 20, 1)])
+@pytest.mark.parametrize("bu", [(0, 1024, 1), (14, 1024, 1), (1 << 20, 1, 0)])
 def test_paper_mode_bcsr_matches_oracle(bu):
     """Binary-search backward lookup in the push, the global relabel and
     the cut BFS, top-down, switched, or bottom-up."""
     m = wb()
-    o = _opts(m, use_rev=0, bottom_up=bu[0], bottom_up_min=bu[1])
+    o = _opts(m, use_rev=0, bottom_up=bu[0], bottom_up_min=bu[1], bottom_up_edges=bu[2])
     for g in (W.rmat(14, 16, 41), W.bipartite_zipf(4096, 4096, 43), W.grid(40, 40, 47)):
         src, dst, cap = g.numpy()
         check_against_oracle(g.n, src, dst, cap, g.s, g.t, "bcsr", o)
