@@ -52,12 +52,13 @@ WORKLOADS = {
 }
 
 # The library's own kernels per step: the BCSR build (half_keys, sorted_caps,
-# scatter_prefix, run_heads, merge_runs, rev_slots, pair_slots,
-# max_degree_kernel; plus count_degrees_warp, iota_u32, invert_order,
-# remap_arcs when the handle is renumbered), solve_kernel for the flow and
-# for the cut, and edge_flow_kernel.  CUB's sort and scan kernels come on top.
+# run_heads, merge_runs, rev_pairs, max_degree_kernel; scatter_prefix only for
+# inputs with parallel arcs, which the R-MAT workloads have not; plus
+# count_degrees_warp, iota_u32, invert_order, remap_arcs when the handle is
+# renumbered), solve_kernel for the flow and for the cut, and
+# edge_flow_kernel.  CUB's sort and scan kernels come on top.
 def launches_per_step(renumbered: bool) -> int:
-    return 11 + (4 if renumbered else 0)
+    return 9 + (4 if renumbered else 0)
 
 
 # Algorithmic bytes per unit of the BCSR solver (each unit is counted by the
@@ -322,8 +323,14 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    opts = None
+    if args.options:
+        opts = wb.wbpr_default_options()
+        for k, v in json.loads(args.options).items():
+            setattr(opts, k, v)
+
     def step():
-        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, wb.WBPR_BCSR, None, stream)
+        G = wb.wbpr_build(n, m, g.src, g.dst, g.cap, s, t, wb.WBPR_BCSR, opts, stream)
         v = wb.wbpr_maxflow(G, stream, flow)
         st = wb.wbpr_get_stats(G)
         c = wb.wbpr_mincut(G, stream, side)
@@ -419,7 +426,7 @@ def run_gpu(args):
               "parallelism": "replicas" if world > 1 else "single",
               "l2": f"inputs larger than L2 (COO {12 * m / 1e6:.0f} MB, BCSR handle "
                     f"{info0['device_bytes'] / 1e6:.0f} MB per step); no flush needed",
-              "flow_value": value_seen,
+              "flow_value": value_seen, "options": json.loads(args.options) if args.options else {},
               "time_to_maxflow_ms": headline["bcsr"]["time_to_maxflow_ms"] if headline else None,
               "resident": headline, "footprint": footprint, "layouts_rmat20": c2}
     gold = golden_rmat26() if args.workload == "rmat26" else None
@@ -673,6 +680,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=512)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0])
     ap.add_argument("--tune", action="store_true", help="batch: per-class tuned knobs, timed again")
+    ap.add_argument("--options", default="",
+                    help='library options of the timed handle as JSON, e.g. {"thread_centric": 1} (profiling)')
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

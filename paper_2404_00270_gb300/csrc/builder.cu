@@ -137,14 +137,15 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
 // between u and v.
 __global__ void merge_runs(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
                            const int *cj, int *col, int *cf0, int *cf, int *cfb, long long *off,
-                           unsigned *slot_by_pos, int *bad)
+                           unsigned *arc2slot, int *bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const u64 mask = (1ull << b) - 1;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
         const unsigned a = slot_of[j] - 1;
         const u64 k = key[j];
-        slot_by_pos[pos[j]] = a;
+        const unsigned p = pos[j];
+        if ((p & 1u) == 0) arc2slot[p >> 1] = a;  // an arc's slot is that of its tail-side half-entry
         const u64 kp = j == 0 ? ~0ull : key[j - 1];
         if (k == kp) continue;
         col[a] = (int)(k & mask);
@@ -171,28 +172,23 @@ __global__ void merge_runs(long long len, int b, const u64 *key, const unsigned 
     }
 }
 
-// BCSR reverse index in slot order: the head of each run (slot a) reads the
-// slot of the other half-entry of one of its arcs (position p ^ 1).
-__global__ void rev_slots(long long len, const u64 *key, const unsigned *pos, const unsigned *slot_of,
-                          const unsigned *slot_by_pos, unsigned *rev)
+// BCSR reverse index: every head-side half-entry (slot a, of arc i) pairs
+// a with the arc's tail-side slot arc2slot[i], both ways.  Every slot holds
+// a half-entry of some arc, on one side or the other, so every slot is
+// written; duplicate arcs write the same values again.
+__global__ void rev_pairs(long long len, const unsigned *pos, const unsigned *slot_of, const unsigned *arc2slot,
+                          unsigned *rev)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
-        if (j > 0 && key[j] == key[j - 1]) continue;
-        rev[slot_of[j] - 1] = slot_by_pos[pos[j] ^ 1u];
+        const unsigned p = pos[j];
+        if ((p & 1u) == 0) continue;
+        const unsigned a = slot_of[j] - 1, t = arc2slot[p >> 1];
+        rev[a] = t;
+        rev[t] = a;
     }
 }
 
-// arc2slot of input arc i is the slot of its tail-side half-entry.
-__global__ void pair_slots(long long m, const int *src, const int *dst, const unsigned *slot_by_pos,
-                           unsigned *arc2slot)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
-        if (src[i] == dst[i]) continue;  // self-loop: no slot
-        arc2slot[i] = slot_by_pos[2 * i];
-    }
-}
 
 // Row ends from sorted row keys: the last slot a of row r writes off[r + 1] =
 // a + 1 (off zeroed before); the max-scan of close_offsets() then fills the
@@ -574,8 +570,6 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             }
         }
         g->slots = S;
-        unsigned *slot_by_pos;
-        BUILD_ALLOC(slot_by_pos, unsigned, 2 * m, pool);
         OWN_ALLOC(g->col, int, S);
         OWN_ALLOC(g->cf, int, S);
         OWN_ALLOC(g->cf0, int, S);
@@ -587,11 +581,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         }
         if (S > 0) {
             merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cj, g->col, g->cf0, g->cf, g->cfb,
-                                                       g->off, slot_by_pos, bad);
+                                                       g->off, g->arc2slot, bad);
             BUILD_CUDA(cudaGetLastError());
             pool.release(cj);
-            if (g->rev) rev_slots<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, heads, slot_by_pos, g->rev);
-            pair_slots<<<grid_for(m), 256, 0, st>>>(m, src, dst, slot_by_pos, g->arc2slot);
+            if (g->rev) rev_pairs<<<grid_for(len), 256, 0, st>>>(len, v2s, heads, g->arc2slot, g->rev);
             BUILD_CUDA(cudaGetLastError());
             wbpr_status rc = close_offsets(g->off);
             if (rc != WBPR_OK) return rc;
