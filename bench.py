@@ -51,14 +51,16 @@ WORKLOADS = {
     "rmat20": dict(scale=20, seed=2, cap_hi=1000),
 }
 
-# The library's own kernels per step: the BCSR build (half_keys, sorted_caps,
-# run_heads, merge_runs, rev_pairs, max_degree_kernel; scatter_prefix only for
-# inputs with parallel arcs, which the R-MAT workloads have not; plus
-# count_degrees_warp, iota_u32, invert_order, remap_arcs when the handle is
-# renumbered), solve_kernel for the flow and for the cut, and
-# edge_flow_kernel.  CUB's sort and scan kernels come on top.
-def launches_per_step(renumbered: bool) -> int:
-    return 9 + (4 if renumbered else 0)
+# The library's own kernels per step: the BCSR build (validate_keys, in_prep,
+# merge_runs4, rev_pairs4, max_degree_kernel; merge_runs and rev_pairs as
+# well when the half-entry count 2m' is not a multiple of four (m' = non-loop
+# arcs; the R-MAT workloads have no self-loops, so m' = m); scatter_prefix
+# only for inputs with parallel arcs, which the R-MAT workloads have not;
+# count_degrees_warp, iota_u32, invert_order when the handle is renumbered),
+# solve_kernel for the flow and for the cut, and edge_flow_kernel.  CUB's
+# sort, merge and scan kernels come on top.
+def launches_per_step(renumbered: bool, m: int) -> int:
+    return 8 + (2 if m % 2 else 0) + (3 if renumbered else 0)
 
 
 # Algorithmic bytes per unit of the BCSR solver (each unit is counted by the
@@ -443,7 +445,7 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel",
                      "launch_ms": launch_ms, "algorithmic_bytes_per_launch": alg_bytes / args.steps,
                      "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"},
-        "gpu_launches": args.steps * launches_per_step(bool(info0["renumbered"])),
+        "gpu_launches": args.steps * launches_per_step(bool(info0["renumbered"]), m),
         "clocks": clocks,
         "e2e": e2e,
     }

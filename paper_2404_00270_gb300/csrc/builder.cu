@@ -2,21 +2,28 @@
 //
 // BCSR (Fig. 2(d)): every non-loop input arc i = (u,v,c) contributes two
 // half-entries, position 2i (row u, col v, capacity c) and position 2i + 1
-// (row v, col u, capacity 0).  One stable radix sort of the half-entries by
-// (row, col) and a merge of equal keys give one slot per neighbour pair with
-// cf0 = sum of the capacities u -> v; rows come out sorted by neighbour id,
-// which the binary-search backward lookup of §3.2 needs.  The positions ride
-// through the sort, so the two half-entries of an arc land in mutually
-// reverse slots (rev[] and arc2slot[] are scatters), and duplicates of (u, v)
-// stay in input order inside their run (the edge-flow split's prefix is a
-// scan by key).
+// (row v, col u, capacity 0).  All half-entries in (row, col) order, ties by
+// position, come from three steps: a radix sort of the arcs by (u, v) (the
+// tail-side half-entries), a stable sort of that list by v alone (the
+// head-side ones, in (v, u) order), and a merge of the two lists.  A merge
+// of equal keys then gives one slot per neighbour pair with cf0 = sum of the
+// capacities u -> v; rows come out sorted by neighbour id, which the
+// binary-search backward lookup of §3.2 needs.  The positions ride along, so
+// the two half-entries of an arc land in mutually reverse slots (rev[] and
+// arc2slot[] are scatters), and duplicates of (u, v) stay in input order
+// inside their run (the edge-flow split's prefix is a scan by key).
 // RCSR (Fig. 2(c)): out rows = arcs sorted by (src, dst); in rows = the same
 // arcs sorted by (dst, src), each in entry keeping flow_idx, the out slot.
 // Keys pack (row, col) into 2 * bitlen(n - 1) bits, so the radix sorts make
-// only as many passes as the vertex count needs.  Sorting and scans use CUB
-// (device radix sort / scan, header-only).
+// only as many passes as the vertex count needs.  Sorting, merging and scans
+// use CUB (device radix sort / merge / scan, header-only).
 #include <cub/cub.cuh>
+#include <cub/device/device_merge.cuh>
+#include <thrust/iterator/counting_iterator.h>
 #include <thrust/iterator/transform_iterator.h>
+#include <thrust/iterator/transform_output_iterator.h>
+#include <thrust/iterator/zip_iterator.h>
+#include <thrust/tuple.h>
 
 #include <stdint.h>
 
@@ -29,8 +36,13 @@ namespace {
 
 typedef unsigned long long u64;
 
+// Arc keys (u << b) | v, self-loops the all-ones key, values the input
+// index; ids are checked before use (flag 1: out of range or negative
+// capacity).  With perm (a renumbered handle) the key holds the new ids
+// perm[u], perm[v].
 __global__ void validate_keys(long long m, int n, int b, u64 loop_key, const int *src, const int *dst,
-                              const int *cap, u64 *key, unsigned *val, int *bad, unsigned long long *nonloop)
+                              const int *cap, const int *perm, u64 *key, unsigned *val, int *bad,
+                              unsigned long long *nonloop)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned long long local = 0;
@@ -39,6 +51,9 @@ __global__ void validate_keys(long long m, int n, int b, u64 loop_key, const int
         if (u < 0 || u >= n || v < 0 || v >= n || c < 0) {
             atomicOr(bad, 1);
             u = v = 0;
+        } else if (perm) {
+            u = __ldg(perm + u);
+            v = __ldg(perm + v);
         }
         if (u != v) {
             key[i] = ((u64)(unsigned)u << b) | (unsigned)v;
@@ -56,53 +71,82 @@ __global__ void validate_keys(long long m, int n, int b, u64 loop_key, const int
 
 // BCSR half-entries: position 2i is input arc i seen from its tail (row u,
 // col v), position 2i + 1 the same arc seen from its head (row v, col u).
-// The stable sort carries the positions along.
-__global__ void half_keys(long long m, int n, int b, u64 loop_key, const int *src, const int *dst, const int *cap,
-                          u64 *key2, unsigned *pos2, int *bad, unsigned long long *nonloop)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    unsigned long long local = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
-        int u = src[i], v = dst[i], c = cap[i];
-        if (u < 0 || u >= n || v < 0 || v >= n || c < 0) {
-            atomicOr(bad, 1);
-            u = v = 0;
-        }
-        if (u != v) {
-            key2[2 * i] = ((u64)(unsigned)u << b) | (unsigned)v;
-            key2[2 * i + 1] = ((u64)(unsigned)v << b) | (unsigned)u;
-            ++local;
-        } else {
-            key2[2 * i] = loop_key;
-            key2[2 * i + 1] = loop_key;
-        }
-        pos2[2 * i] = (unsigned)(2 * i);
-        pos2[2 * i + 1] = (unsigned)(2 * i + 1);
-    }
-    typedef cub::BlockReduce<unsigned long long, 256> Reduce;
-    __shared__ typename Reduce::TempStorage tmp;
-    local = Reduce(tmp).Sum(local);
-    if (threadIdx.x == 0 && local) atomicAdd(nonloop, local);
-}
+// The arcs sorted by (u, v) are the tail-side half-entries in order; a
+// stable sort of that list by v gives the head-side ones in order, and a
+// merge of the two lists by (key, position) gives every half-entry in the
+// order of one stable sort by key.
 
-// Capacity of each sorted half-entry's arc, in sorted order: c on its tail
-// side, -(c + 1) on its head side (c >= 0), so that later passes read both
-// sums of a run sequentially instead of gathering cap[] again.
-// Also flags (dup = 1) a parallel arc: two tail-side half-entries with the
-// same key, the only case that needs the duplicate prefix.
-__global__ void sorted_caps(long long len, const u64 *key, const unsigned *pos, const int *cap, int *out,
-                            int *dup)
+// Head-side list entry: the arc's tail, its input index and its capacity.
+struct InVal {
+    unsigned u;
+    unsigned i;
+    int c;
+};
+
+// Keys and values of the head-side sort from the (u, v)-sorted arcs k < mp
+// (self-loops sorted after them).  Also flags (dup = 1) a parallel arc: two
+// equal neighbouring keys, the only case that needs the duplicate prefix.
+__global__ void in_prep(long long mp, int b, const u64 *key, const unsigned *val, const int *cap, unsigned *kin,
+                        InVal *vin, int *dup)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
-        const unsigned p = pos[j];
-        const int c = cap[p >> 1];
-        out[j] = (p & 1u) ? -c - 1 : c;
-        if (j > 0 && (p & 1u) == 0 && key[j] == key[j - 1] && (pos[j - 1] & 1u) == 0) *dup = 1;
+    const u64 mask = (1ull << b) - 1;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < mp; k += stride) {
+        const u64 x = key[k];
+        const unsigned i = val[k];
+        kin[k] = (unsigned)(x & mask);
+        vin[k] = InVal{(unsigned)(x >> b), i, cap[i]};
+        if (k > 0 && key[k - 1] == x) *dup = 1;
     }
 }
 
-// The tail-side capacity of a sorted_caps() entry (0 on the head side).
+// One half-entry as the merge sees it: packed (row, col) key, position, and
+// capacity (c on the tail side, -(c + 1) on the head side, c >= 0).
+struct HalfRec {
+    u64 k;
+    unsigned p;
+    int c;
+};
+
+struct HalfLess {
+    __host__ __device__ bool operator()(const HalfRec &a, const HalfRec &b) const
+    {
+        return a.k < b.k || (a.k == b.k && a.p < b.p);
+    }
+};
+
+// k-th tail-side half-entry.
+struct OutHalf {
+    const u64 *key;
+    const unsigned *val;
+    const int *cap;
+    __host__ __device__ HalfRec operator()(long long k) const
+    {
+        const unsigned i = val[k];
+        return HalfRec{key[k], 2u * i, cap[i]};
+    }
+};
+
+// q-th head-side half-entry.
+struct InHalf {
+    int b;
+    const unsigned *kin;
+    const InVal *vin;
+    __host__ __device__ HalfRec operator()(long long q) const
+    {
+        const InVal x = vin[q];
+        return HalfRec{((u64)kin[q] << b) | x.u, 2u * x.i + 1u, -x.c - 1};
+    }
+};
+
+struct SplitHalf {
+    __host__ __device__ thrust::tuple<u64, unsigned, int> operator()(const HalfRec &r) const
+    {
+        return thrust::make_tuple(r.k, r.p, r.c);
+    }
+};
+
+// The tail-side capacity of a merged capacity entry (0 on the head side).
 struct TailPart {
     __host__ __device__ int operator()(int x) const { return x > 0 ? x : 0; }
 };
@@ -116,12 +160,14 @@ __global__ void scatter_prefix(long long len, const unsigned *pos, const int *pr
     }
 }
 
-__global__ void run_heads(long long len, const u64 *key, unsigned *head)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride)
-        head[j] = (j == 0 || key[j] != key[j - 1]) ? 1u : 0u;
-}
+// 1 where a run of equal keys starts (the scan's input, read on the fly).
+struct RunHead {
+    const u64 *key;
+    __host__ __device__ unsigned operator()(long long j) const
+    {
+        return (j == 0 || key[j] != key[j - 1]) ? 1u : 0u;
+    }
+};
 
 // slot_of = inclusive scan of run heads (1-based slot numbers).  Every
 // half-entry records its slot; the head of each run (one neighbour pair seen
@@ -135,40 +181,69 @@ __global__ void run_heads(long long len, const u64 *key, unsigned *head)
 // to the other, and with the mirror (cfb != null) it is the initial cfb.
 // Runs are short: one per (u, v), as long as the number of duplicate arcs
 // between u and v.
-__global__ void merge_runs(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
-                           const int *cj, int *col, int *cf0, int *cf, int *cfb, long long *off,
-                           unsigned *arc2slot, int *bad)
+struct RunOut {
+    int *col, *cf0, *cf, *cfb;
+    long long *off;
+    unsigned *arc2slot;
+    int *bad;
+};
+
+// Half-entry j (key k, position p, slot a; kp the key before it).
+__device__ __forceinline__ void merge_one(long long j, long long len, int b, u64 k, u64 kp, unsigned p, unsigned a,
+                                          const u64 *key, const int *cj, const RunOut &o)
+{
+    if ((p & 1u) == 0) o.arc2slot[p >> 1] = a;  // an arc's slot is that of its tail-side half-entry
+    if (k == kp) return;
+    o.col[a] = (int)(k & ((1ull << b) - 1));
+    long long sum = 0, back = 0;
+    long long i = j;
+    for (; i < len && key[i] == k; ++i) {
+        const int x = cj[i];
+        if (x >= 0) sum += x;
+        else back += -(long long)x - 1;
+    }
+    const long long r = (long long)(k >> b);
+    if (i == len || (long long)(key[i] >> b) != r) o.off[r + 1] = (long long)a + 1;
+    if (sum > 0x7fffffffLL) {
+        atomicOr(o.bad, 2);
+        sum = 0;
+    }
+    if (sum + back > 0x7fffffffLL) {
+        atomicOr(o.bad, 4);
+        back = 0;
+    }
+    o.cf0[a] = (int)sum;
+    o.cf[a] = (int)sum;
+    if (o.cfb) o.cfb[a] = (int)back;
+}
+
+// Half-entries start..len-1, one per thread and step.
+__global__ void merge_runs(long long start, long long len, int b, const u64 *key, const unsigned *pos,
+                           const unsigned *slot_of, const int *cj, RunOut o)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const u64 mask = (1ull << b) - 1;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
-        const unsigned a = slot_of[j] - 1;
-        const u64 k = key[j];
-        const unsigned p = pos[j];
-        if ((p & 1u) == 0) arc2slot[p >> 1] = a;  // an arc's slot is that of its tail-side half-entry
+    for (long long j = start + blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride)
+        merge_one(j, len, b, key[j], j == 0 ? ~0ull : key[j - 1], pos[j], slot_of[j] - 1, key, cj, o);
+}
+
+// Half-entries 0..4 * (len / 4) - 1, four consecutive ones per thread and
+// step, with 16-byte loads (key, pos, slot_of 16-byte aligned).
+__global__ void merge_runs4(long long len, int b, const u64 *key, const unsigned *pos, const unsigned *slot_of,
+                            const int *cj, RunOut o)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = len >> 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const ulonglong2 k01 = reinterpret_cast<const ulonglong2 *>(key)[2 * q];       // the run loop
+        const ulonglong2 k23 = reinterpret_cast<const ulonglong2 *>(key)[2 * q + 1];   // reads these again
+        const uint4 p4 = __ldcs(reinterpret_cast<const uint4 *>(pos) + q);
+        const uint4 s4 = __ldcs(reinterpret_cast<const uint4 *>(slot_of) + q);
+        const long long j = 4 * q;
         const u64 kp = j == 0 ? ~0ull : key[j - 1];
-        if (k == kp) continue;
-        col[a] = (int)(k & mask);
-        long long sum = 0, back = 0;
-        long long i = j;
-        for (; i < len && key[i] == k; ++i) {
-            const int x = cj[i];
-            if (x >= 0) sum += x;
-            else back += -(long long)x - 1;
-        }
-        const long long r = (long long)(k >> b);
-        if (i == len || (long long)(key[i] >> b) != r) off[r + 1] = (long long)a + 1;
-        if (sum > 0x7fffffffLL) {
-            atomicOr(bad, 2);
-            sum = 0;
-        }
-        if (sum + back > 0x7fffffffLL) {
-            atomicOr(bad, 4);
-            back = 0;
-        }
-        cf0[a] = (int)sum;
-        cf[a] = (int)sum;
-        if (cfb) cfb[a] = (int)back;
+        merge_one(j, len, b, k01.x, kp, p4.x, s4.x - 1, key, cj, o);
+        merge_one(j + 1, len, b, k01.y, k01.x, p4.y, s4.y - 1, key, cj, o);
+        merge_one(j + 2, len, b, k23.x, k01.y, p4.z, s4.z - 1, key, cj, o);
+        merge_one(j + 3, len, b, k23.y, k23.x, p4.w, s4.w - 1, key, cj, o);
     }
 }
 
@@ -176,11 +251,11 @@ __global__ void merge_runs(long long len, int b, const u64 *key, const unsigned 
 // a with the arc's tail-side slot arc2slot[i], both ways.  Every slot holds
 // a half-entry of some arc, on one side or the other, so every slot is
 // written; duplicate arcs write the same values again.
-__global__ void rev_pairs(long long len, const unsigned *pos, const unsigned *slot_of, const unsigned *arc2slot,
-                          unsigned *rev)
+__global__ void rev_pairs(long long start, long long len, const unsigned *pos, const unsigned *slot_of,
+                          const unsigned *arc2slot, unsigned *rev)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
+    for (long long j = start + blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
         const unsigned p = pos[j];
         if ((p & 1u) == 0) continue;
         const unsigned a = slot_of[j] - 1, t = arc2slot[p >> 1];
@@ -189,6 +264,31 @@ __global__ void rev_pairs(long long len, const unsigned *pos, const unsigned *sl
     }
 }
 
+// Half-entries 0..4 * (len / 4) - 1, four consecutive ones per thread and
+// step (16-byte loads of pos and slot_of): their gathers from arc2slot are
+// independent, so up to four are in flight per thread.
+__global__ void rev_pairs4(long long len, const unsigned *pos, const unsigned *slot_of, const unsigned *arc2slot,
+                           unsigned *rev)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = len >> 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const uint4 p4 = __ldcs(reinterpret_cast<const uint4 *>(pos) + q);
+        const uint4 s4 = __ldcs(reinterpret_cast<const uint4 *>(slot_of) + q);
+        const unsigned p[4] = {p4.x, p4.y, p4.z, p4.w};
+        const unsigned a[4] = {s4.x - 1, s4.y - 1, s4.z - 1, s4.w - 1};
+        unsigned t[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (p[e] & 1u) t[e] = __ldcg(arc2slot + (p[e] >> 1));
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (p[e] & 1u) {
+                rev[a[e]] = t[e];
+                rev[t[e]] = a[e];
+            }
+    }
+}
 
 // Row ends from sorted row keys: the last slot a of row r writes off[r + 1] =
 // a + 1 (off zeroed before); the max-scan of close_offsets() then fills the
@@ -450,13 +550,20 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         pool.release(ids);
         pool.release(degs);
         pool.release(deg);
-        int *perm, *rsrc, *rdst;
+        int *perm;
         OWN_ALLOC(g->perm, int, n);
         perm = g->perm;
-        BUILD_ALLOC(rsrc, int, m, pool);
-        BUILD_ALLOC(rdst, int, m, pool);
         invert_order<<<grid_for(n), 256, 0, st>>>(n, g->order, perm);
-        remap_arcs<<<grid_for(m), 256, 0, st>>>(m, perm, src, dst, rsrc, rdst);
+        if (g->layout != WBPR_BCSR) {
+            // RCSR reads the renumbered endpoints more than once; BCSR's key
+            // pass maps them itself
+            int *rsrc, *rdst;
+            BUILD_ALLOC(rsrc, int, m, pool);
+            BUILD_ALLOC(rdst, int, m, pool);
+            remap_arcs<<<grid_for(m), 256, 0, st>>>(m, perm, src, dst, rsrc, rdst);
+            src = rsrc;
+            dst = rdst;
+        }
         BUILD_CUDA(cudaGetLastError());
         int st_int[2];
         BUILD_CUDA(cudaMemcpyAsync(&st_int[0], perm + g->s, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -464,8 +571,6 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_CUDA(cudaStreamSynchronize(st));
         g->s_int = st_int[0];
         g->t_int = st_int[1];
-        src = rsrc;
-        dst = rdst;
     }
 
     OWN_ALLOC(g->arc2slot, unsigned, m);
@@ -485,15 +590,16 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
     BUILD_CUDA(cudaMemsetAsync(g->arc2slot, 0xff, sizeof(unsigned) * (size_t)(m > 0 ? m : 1), st));
 
     if (g->layout == WBPR_BCSR) {
-        // ---- both half-entries of every arc, one stable sort ---------------------
-        u64 *k2, *k2b;
-        unsigned *v2, *v2b;
-        BUILD_ALLOC(k2, u64, 2 * m, pool);
-        BUILD_ALLOC(k2b, u64, 2 * m, pool);
-        BUILD_ALLOC(v2, unsigned, 2 * m, pool);
-        BUILD_ALLOC(v2b, unsigned, 2 * m, pool);
+        // ---- tail-side order: the arcs sorted by (u, v) ------------------------------
+        u64 *ko, *kob;
+        unsigned *vo, *vob;
+        BUILD_ALLOC(ko, u64, m, pool);
+        BUILD_ALLOC(kob, u64, m, pool);
+        BUILD_ALLOC(vo, unsigned, m, pool);
+        BUILD_ALLOC(vob, unsigned, m, pool);
         if (m > 0) {
-            half_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, loop_key, src, dst, cap, k2, v2, bad, counter);
+            validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, loop_key, src, dst, cap, g->perm, ko, vo, bad,
+                                                       counter);
             BUILD_CUDA(cudaGetLastError());
         }
         BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -502,50 +608,97 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         if (h_bad) return set_error(WBPR_EINVAL, "build: vertex id out of range or negative capacity");
         const long long mp = (long long)h_nonloop;
         g->mprime = mp;
-        cub::DoubleBuffer<u64> dk2(k2, k2b);
-        cub::DoubleBuffer<unsigned> dv2(v2, v2b);
+        cub::DoubleBuffer<u64> dko(ko, kob);
+        cub::DoubleBuffer<unsigned> dvo(vo, vob);
         if (m > 0) {
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk2, dv2, (int64_t)(2 * m), 0, end_bit, st));
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dko, dvo, (int64_t)m, 0, end_bit, st));
             void *t3 = pool.get(nb);
             if (!t3) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t3, nb, dk2, dv2, (int64_t)(2 * m), 0, end_bit, st));
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t3, nb, dko, dvo, (int64_t)m, 0, end_bit, st));
             pool.release(t3);
         }
-        u64 *k2s = dk2.Current();
-        unsigned *v2s = dv2.Current();
-        pool.release(k2s == k2 ? k2b : k2);
-        pool.release(v2s == v2 ? v2b : v2);
-        const long long len = 2 * mp;  // the self-loops' entries sort after these
+        u64 *kos = dko.Current();
+        unsigned *vos = dvo.Current();
+        pool.release(kos == ko ? kob : ko);
+        pool.release(vos == vo ? vob : vo);
+        const long long len = 2 * mp;  // self-loops sort last and get no half-entries
+
+        // ---- head-side order: the same arcs stably sorted by v ------------------------
+        // Stable over the (u, v) order, so the result is the (v, u) order with
+        // duplicates still in input order.  Tail, input index and capacity ride
+        // along, so no later pass gathers them.
+        int *dup = bad + 2;   // zeroed with the other flags
+        unsigned *kin = nullptr, *kinb = nullptr;
+        InVal *vin = nullptr, *vinb = nullptr;
+        BUILD_ALLOC(kin, unsigned, mp, pool);
+        BUILD_ALLOC(kinb, unsigned, mp, pool);
+        BUILD_ALLOC(vin, InVal, mp, pool);
+        BUILD_ALLOC(vinb, InVal, mp, pool);
+        cub::DoubleBuffer<unsigned> dki(kin, kinb);
+        cub::DoubleBuffer<InVal> dvi(vin, vinb);
+        if (mp > 0) {
+            in_prep<<<grid_for(mp), 256, 0, st>>>(mp, kb, kos, vos, cap, kin, vin, dup);
+            BUILD_CUDA(cudaGetLastError());
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dki, dvi, (int64_t)mp, 0, kb, st));
+            void *t6 = pool.get(nb);
+            if (!t6) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t6, nb, dki, dvi, (int64_t)mp, 0, kb, st));
+            pool.release(t6);
+        }
+        unsigned *kis = dki.Current();
+        InVal *vis = dvi.Current();
+        pool.release(kis == kin ? kinb : kin);
+        pool.release(vis == vin ? vinb : vin);
+
+        // ---- both half-entries in (row, col) order: merge the two lists --------------
+        // Records compare by (key, position); positions are unique (2i tail side,
+        // 2i + 1 head side), so the merge is the stable sort of all half-entries
+        // by key.  Outputs: sorted keys, positions, and capacities (c on the tail
+        // side, -(c + 1) on the head side).
+        u64 *k2s = nullptr;
+        unsigned *v2s = nullptr;
+        int *cj = nullptr;
+        BUILD_ALLOC(k2s, u64, len, pool);
+        BUILD_ALLOC(v2s, unsigned, len, pool);
+        BUILD_ALLOC(cj, int, len, pool);
+        if (len > 0) {
+            auto in1 = thrust::make_transform_iterator(thrust::counting_iterator<long long>(0), OutHalf{kos, vos, cap});
+            auto in2 = thrust::make_transform_iterator(thrust::counting_iterator<long long>(0), InHalf{kb, kis, vis});
+            auto out = thrust::make_transform_output_iterator(thrust::make_zip_iterator(k2s, v2s, cj), SplitHalf{});
+            size_t nb = 0;
+            BUILD_CUDA(cub::DeviceMerge::MergeKeys(nullptr, nb, in1, (int64_t)mp, in2, (int64_t)mp, out, HalfLess{},
+                                                   st));
+            void *t7 = pool.get(nb);
+            if (!t7) return set_error(WBPR_ENOMEM, "build: device allocation failed");
+            BUILD_CUDA(cub::DeviceMerge::MergeKeys(t7, nb, in1, (int64_t)mp, in2, (int64_t)mp, out, HalfLess{}, st));
+            pool.release(t7);
+        }
+        pool.release(kis);
+        pool.release(vis);
+        pool.release(kos);
+        pool.release(vos);
 
         // ---- duplicate prefix (edge-flow split in input order) ------------------
-        // The sort is stable and positions grow with the input order, so the
-        // tail-side half-entries of duplicates of (u, v) sit in input order in
-        // one run: an exclusive sum by key over their capacities.
+        // The tail-side half-entries of duplicates of (u, v) sit in input order
+        // in one run: an exclusive sum by key over their capacities.
         OWN_ALLOC(g->prefix, int, m);
         OWN_ALLOC(g->cap_in, int, m);
         if (m > 0) BUILD_CUDA(cudaMemcpyAsync(g->cap_in, cap, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st));
         BUILD_CUDA(cudaMemsetAsync(g->prefix, 0, sizeof(int) * (size_t)(m > 0 ? m : 1), st));
-        int *cj = nullptr;
-        int *dup = bad + 2;   // zeroed with the other flags
-        if (len > 0) {
-            BUILD_ALLOC(cj, int, len, pool);
-            sorted_caps<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, cap, cj, dup);
-            BUILD_CUDA(cudaGetLastError());
-        }
 
         // ---- merge runs into slots ------------------------------------------------
         unsigned *heads;
         BUILD_ALLOC(heads, unsigned, len, pool);
         unsigned S = 0;
         if (len > 0) {
-            run_heads<<<grid_for(len), 256, 0, st>>>(len, k2s, heads);
-            BUILD_CUDA(cudaGetLastError());
+            auto flags = thrust::make_transform_iterator(thrust::counting_iterator<long long>(0), RunHead{k2s});
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceScan::InclusiveSum(nullptr, nb, heads, heads, (int64_t)len, st));
+            BUILD_CUDA(cub::DeviceScan::InclusiveSum(nullptr, nb, flags, heads, (int64_t)len, st));
             void *t4 = pool.get(nb);
             if (!t4) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceScan::InclusiveSum(t4, nb, heads, heads, (int64_t)len, st));
+            BUILD_CUDA(cub::DeviceScan::InclusiveSum(t4, nb, flags, heads, (int64_t)len, st));
             pool.release(t4);
             BUILD_CUDA(cudaMemcpyAsync(&S, heads + (len - 1), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
             int h_dup = 0;
@@ -580,11 +733,22 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             OWN_ALLOC(g->cfb, int, S);
         }
         if (S > 0) {
-            merge_runs<<<grid_for(len), 256, 0, st>>>(len, kb, k2s, v2s, heads, cj, g->col, g->cf0, g->cf, g->cfb,
-                                                       g->off, g->arc2slot, bad);
+            const RunOut ro{g->col, g->cf0, g->cf, g->cfb, g->off, g->arc2slot, bad};
+            // four half-entries per thread where the streamed arrays allow
+            // 16-byte loads, the remainder (and any unaligned case) one each
+            const bool a16 = ((reinterpret_cast<uintptr_t>(k2s) | reinterpret_cast<uintptr_t>(v2s) |
+                               reinterpret_cast<uintptr_t>(heads)) & 15) == 0;
+            const long long done = a16 ? (len & ~3LL) : 0;
+            if (done) merge_runs4<<<grid_for(done / 4), 256, 0, st>>>(len, kb, k2s, v2s, heads, cj, ro);
+            if (len > done)
+                merge_runs<<<grid_for(len - done), 256, 0, st>>>(done, len, kb, k2s, v2s, heads, cj, ro);
             BUILD_CUDA(cudaGetLastError());
             pool.release(cj);
-            if (g->rev) rev_pairs<<<grid_for(len), 256, 0, st>>>(len, v2s, heads, g->arc2slot, g->rev);
+            if (g->rev) {
+                if (done) rev_pairs4<<<grid_for(done / 4), 256, 0, st>>>(len, v2s, heads, g->arc2slot, g->rev);
+                if (len > done)
+                    rev_pairs<<<grid_for(len - done), 256, 0, st>>>(done, len, v2s, heads, g->arc2slot, g->rev);
+            }
             BUILD_CUDA(cudaGetLastError());
             wbpr_status rc = close_offsets(g->off);
             if (rc != WBPR_OK) return rc;
@@ -604,8 +768,8 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_ALLOC(val1, unsigned, m, pool);
         BUILD_ALLOC(val1b, unsigned, m, pool);
         if (m > 0) {
-            validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, loop_key, src, dst, cap, key1, val1, bad,
-                                                       counter);
+            validate_keys<<<grid_for(m), 256, 0, st>>>(m, (int)n, kb, loop_key, src, dst, cap, nullptr, key1, val1,
+                                                       bad, counter);
             BUILD_CUDA(cudaGetLastError());
         }
         BUILD_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
