@@ -1899,7 +1899,7 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
             bfs_level_bu<L, kBfsBackward>(c, base + level + 1);
         else
             bfs_level<L, kBfsBackward, SW>(c, base + level + 1);
-        if (!grid_sync(c, 11)) return false;
+        if (!grid_sync(c, bu_mode ? 13 : 11)) return false;  // trace id: bottom-up or top-down level
         c.gen++;
     }
     long long wo = 0, nd = 0, nde = 0;
@@ -2133,11 +2133,12 @@ __device__ bool min_cut(Ctx &c)
         seen += tot;
         const long long fe = __ldcg(&P.st.ctl->fedges[c.gen % 3]);
         unseen_edges -= fe;
-        if (bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen))
+        const bool bu_mode = bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen);
+        if (bu_mode)
             bfs_level_bu<L, kBfsForward>(c, level + 2);
         else
             bfs_level<L, kBfsForward, SW>(c, level + 2);
-        if (!grid_sync(c, 31)) return false;
+        if (!grid_sync(c, bu_mode ? 34 : 31)) return false;  // trace id: bottom-up or top-down level
         c.gen++;
     }
     long long sum = 0;
