@@ -139,6 +139,12 @@ typedef struct wbpr_options {
                                  entries of the frontier, times bottom_up, with
                                  those of the vertices not yet visited; 0 = compare
                                  vertex counts (default) */
+    int32_t avq_incremental;  /* 1 = between two global relabels, build the AVQ only
+                                 from the vertices the last pass pushed into or left
+                                 with excess (a bitmap the pushes mark); the first
+                                 compaction after a global relabel, and one that
+                                 applies a gap, scan every vertex (default).  0 =
+                                 every compaction scans every vertex (Alg. 2). */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */

@@ -67,7 +67,8 @@ class Options(ctypes.Structure):
                 ("bottom_up", ctypes.c_int32), ("bottom_up_min", ctypes.c_int32),
                 ("renumber", ctypes.c_int32), ("thread_centric", ctypes.c_int32),
                 ("warp_time", ctypes.c_int32), ("stage_hubs", ctypes.c_int32),
-                ("barrier_extra", ctypes.c_int32), ("bottom_up_edges", ctypes.c_int32)]
+                ("barrier_extra", ctypes.c_int32), ("bottom_up_edges", ctypes.c_int32),
+                ("avq_incremental", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -106,6 +106,7 @@ void wbpr_default_options(wbpr_options *o)
     o->stage_hubs = 0;
     o->barrier_extra = 0;
     o->bottom_up_edges = 0;
+    o->avq_incremental = 1;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -156,6 +157,7 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->barrier_extra < 0 || o->barrier_extra > 1024) return WBPR_EINVAL;
     if (o->stage_hubs != 0 && o->stage_hubs != 1) return WBPR_EINVAL;
     if (o->bottom_up_edges != 0 && o->bottom_up_edges != 1) return WBPR_EINVAL;
+    if (o->avq_incremental != 0 && o->avq_incremental != 1) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -201,6 +203,7 @@ static wbpr_status alloc_state(wbpr_graph *g, cudaStream_t st)
         STATE_ALLOC(g->hub_aux[a], unsigned long long, n);
         STATE_ALLOC(g->hub_done[a], unsigned, n);
     }
+    STATE_ALLOC(g->touch, unsigned, (n + 31) / 32);
     STATE_ALLOC(g->ctl, Ctl, 1);
     int per_sm = 0;
     API_CUDA(solver_max_blocks_per_sm(g->layout, 8, &per_sm));
@@ -437,6 +440,8 @@ Params make_params(wbpr_graph *g, int mode)
         p.st.hub_aux[a] = g->hub_aux[a];
         p.st.hub_done[a] = g->hub_done[a];
     }
+    // (the thread-centric baseline builds no AVQ: its pushes mark nothing)
+    p.st.touch = (g->opts.avq_incremental && !g->opts.thread_centric) ? g->touch : nullptr;
     p.st.ctl = g->ctl;
     p.st.bstats = g->bstats;
     p.mode = mode;

@@ -73,6 +73,7 @@ struct wbpr_graph {
     long long *hub_rem[2] = {nullptr, nullptr};
     unsigned long long *hub_aux[2] = {nullptr, nullptr};
     unsigned *hub_done[2] = {nullptr, nullptr};
+    unsigned *touch = nullptr;
     wbpr::Ctl *ctl = nullptr;
     long long *bstats = nullptr;
     unsigned long long *trace = nullptr;  // optional barrier trace (wbpr_options.trace)

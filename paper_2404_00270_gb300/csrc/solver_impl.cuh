@@ -494,6 +494,15 @@ __device__ __forceinline__ long long lower_bound_col(const int *col, long long b
     return b;
 }
 
+// Marks v as a candidate of the next AVQ (incremental compaction): a
+// fire-and-forget atomic OR on v's bitmap word.  Pushes mark their target,
+// and an owner that keeps excess after its pass marks itself, so every
+// vertex that can be active after a pass is marked.
+__device__ __forceinline__ void touch_mark(const StateDev &st, int v)
+{
+    if (st.touch) atomicOr(st.touch + (v >> 5), 1u << (v & 31));
+}
+
 // Relabel u from hu to hn (capped at hcap) and keep the gap counts.
 __device__ __forceinline__ void relabel_to(Ctx &c, int u, int hu, int hn, bool phase1, int hcap)
 {
@@ -569,13 +578,16 @@ __device__ void apply_op(Ctx &c, int u, u64 key, bool phase1, int hcap)
                     atomicSub(g.cfb + mir_ra, (int)d);
                 }
                 atomicAdd((u64 *)(e + v), (u64)d);
+                touch_mark(P.st, v);
                 atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], 1ull);
             }
+            if (eu > d) touch_mark(P.st, u);
             return;
         }
     }
     int hn = (key == kNoKey) ? hcap : (int)(key >> 32) + 1;
     relabel_to(c, u, hu, hn, phase1, hcap);
+    touch_mark(P.st, u);
 }
 
 // Tile of W <= 32 lanes (all 32 lanes of the warp call this; u < 0 = idle).
@@ -693,6 +705,7 @@ __device__ __forceinline__ void mp_push(const Params &P, int u, long long k, boo
     atomicSub(dec, d);
     atomicAdd(inc, d);
     atomicAdd((u64 *)(P.st.e + v), (u64)(long long)d);
+    touch_mark(P.st, v);
 }
 
 template <int L, int W>
@@ -787,7 +800,10 @@ __device__ void mp_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
         if (D > 0) atomicAdd((u64 *)(P.st.e + u), (u64)(-D));
         if (npush) atomicAdd((unsigned long long *)&c.sm.stats[kStatPushes], (u64)npush);
         atomicAdd((unsigned long long *)&c.sm.stats[kStatArcs], (u64)scanned);
-        if (rem > 0) relabel_to(c, u, hu, hres == 0x7fffffff ? hcap : hres + 1, phase1, hcap);
+        if (rem > 0) {
+            relabel_to(c, u, hu, hres == 0x7fffffff ? hcap : hres + 1, phase1, hcap);
+            touch_mark(P.st, u);
+        }
     }
 }
 
@@ -803,7 +819,13 @@ struct WGrab {
 __device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks, WGrab &gb,
                                             unsigned &pos, unsigned &j, unsigned &nch)
 {
-    if (gb.next >= gb.end) {
+    if (nchunks <= c.nblk * kWarps) {
+        // no more chunks than warps: warp gw takes chunk gw, without an atomic
+        const unsigned gw = c.bid * kWarps + (threadIdx.x >> 5);
+        if (gb.end != 0 || gw >= nchunks) return false;
+        gb.end = 1;
+        gb.next = gw;
+    } else if (gb.next >= gb.end) {
         unsigned b = 0;
         if ((threadIdx.x & 31) == 0) b = atomicAdd(&c.P.st.ctl->q_grab[s3], gb.batch);
         b = __shfl_sync(kFull, b, 0);
@@ -829,10 +851,17 @@ __device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh
 
 // Rows of the warp class, taken dynamically by warps in batches of `batch`
 // (one atomic per batch): the next row index for the calling warp, or
-// `count` when none is left.  Warp-uniform.
+// `count` when none is left.  With no more rows than warps (nwarps), warp gw
+// takes row gw, without an atomic: thousands of warps meeting on one counter
+// would cost more than the few rows.  Warp-uniform; next = end = 0 at first.
 __device__ __forceinline__ unsigned grab_rows(unsigned *ctr, unsigned count, unsigned batch, unsigned &next,
-                                              unsigned &end)
+                                              unsigned &end, unsigned gw, unsigned nwarps)
 {
+    if (count <= nwarps) {
+        const unsigned r = end == 0 && gw < count ? gw : count;
+        end = 1;
+        return r;
+    }
     if (next >= end) {
         unsigned b = 0;
         if ((threadIdx.x & 31) == 0) b = atomicAdd(ctr, batch);
@@ -1012,7 +1041,10 @@ __device__ void pr_wchunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nc
                 const long long rem = __ldcg(P.st.hub_rem[set] + pos);
                 const long long D = __ldcg(P.st.hub_e0[set] + pos) - rem;
                 if (D > 0) atomicAdd((u64 *)(P.st.e + u), (u64)(-D));
-                if (rem > 0) relabel_to(c, u, hu, key == kNoKey ? hcap : (int)(key >> 32) + 1, phase1, hcap);
+                if (rem > 0) {
+                    relabel_to(c, u, hu, key == kNoKey ? hcap : (int)(key >> 32) + 1, phase1, hcap);
+                    touch_mark(P.st, u);
+                }
             }
         }
     }
@@ -1054,7 +1086,7 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
         const unsigned batch = c1 / (8u * nwarps) + 1u;
         unsigned next = 0, end = 0;
         for (;;) {
-            const unsigned i = grab_rows(&ctl->q_grab_w[s3], c1, batch, next, end);
+            const unsigned i = grab_rows(&ctl->q_grab_w[s3], c1, batch, next, end, gwarp, nwarps);
             if (i >= c1) break;
             if (P.multi_push) mp_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
             else pr_tile<L, 32>(c, __ldcg(q1 + i), lane, phase1, hcap);
@@ -1166,9 +1198,87 @@ __device__ void tc_process(Ctx &c, bool phase1, int hcap)
     warp_clock_add(c, wt0);
 }
 
-// Step 1 of an iteration: build the AVQ of generation `gen`.
+// Incremental compaction: between two global relabels a vertex can turn
+// active only by receiving a push (its height only grows, its excess only
+// grows through pushes), and an active vertex stays active only if its owner
+// left excess after its pass; both mark the vertex in the candidate bitmap.
+// So the AVQ is the set of marked vertices with e > 0 and h below the cap.
+// Warps take 32 bitmap words (1,024 vertices) at a time and clear them; the
+// marked vertices of the 32 words are dealt to the lanes 32 at a time (a
+// warp scan of the words' bit counts; each lane finds the word and the bit
+// of its candidate), ballots rank the active ones per tile class, and one
+// atomic per class and round places them.
 template <int L>
-__device__ void build_avq(Ctx &c, bool phase1, int hcap)
+__device__ void build_avq_inc(Ctx &c, int hcap)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int s = g.s, t = g.t;
+    const int gen = c.gen, s3 = gen % 3, set = gen & 1;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long nwords = ((long long)g.n + 31) >> 5;
+    const long long gwarp = (long long)c.bid * kWarps + (threadIdx.x >> 5);
+    const long long nwarps = (long long)c.nblk * kWarps;
+    long long nact = 0;
+    for (long long w0 = gwarp * 32; w0 < nwords; w0 += nwarps * 32) {
+        const long long w = w0 + lane;
+        const unsigned bits = w < nwords ? __ldcg(P.st.touch + w) : 0u;
+        if (bits) __stcg(P.st.touch + w, 0u);
+        const unsigned cnt = __popc(bits);
+        unsigned incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        for (unsigned r0 = 0; r0 < total; r0 += 32) {
+            const unsigned k = r0 + lane;  // this lane's candidate: the k-th marked vertex of the words
+            unsigned src = 0;              // its word: lanes whose inclusive count is <= k
+#pragma unroll
+            for (unsigned b = 16; b > 0; b >>= 1) {
+                const unsigned x = __shfl_sync(kFull, incl, src + b - 1);
+                if (x <= k) src += b;
+            }
+            const unsigned sl = src < 32 ? src : 31;
+            unsigned word = __shfl_sync(kFull, bits, sl);
+            const unsigned before = __shfl_sync(kFull, incl, sl) - __shfl_sync(kFull, cnt, sl);
+            int v = -1;
+            if (k < total) {
+                for (unsigned i = before; i < k; ++i) word &= word - 1;  // drop the bits before it
+                v = (int)((w0 + sl) * 32 + (__ffs(word) - 1));
+            }
+            long long ev = 0, d = 0;
+            int cls = -1;
+            if (v >= 0 && v != s && v != t && __ldcg(P.st.h + v) < hcap) {
+                ev = __ldcg(P.st.e + v);
+                if (ev > 0) {
+                    d = degree<L>(g, v);
+                    cls = classify(P, d);
+                    ++nact;
+                }
+            }
+            warp_hub_append<L>(c, s3, set, cls == 2, v, d, ev);
+            const unsigned m0 = __ballot_sync(kFull, cls == 0), m1 = __ballot_sync(kFull, cls == 1);
+            unsigned b0 = 0, b1 = 0;
+            if (lane == 0 && m0) b0 = atomicAdd(&P.st.ctl->q_count[s3][0], (unsigned)__popc(m0));
+            if (lane == 0 && m1) b1 = atomicAdd(&P.st.ctl->q_count[s3][1], (unsigned)__popc(m1));
+            b0 = __shfl_sync(kFull, b0, 0);
+            b1 = __shfl_sync(kFull, b1, 0);
+            if (cls == 0) P.st.q[set][0][b0 + __popc(m0 & lt)] = v;
+            if (cls == 1) P.st.q[set][1][b1 + __popc(m1 & lt)] = v;
+        }
+    }
+    if (nact) atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)nact);
+}
+
+// Step 1 of an iteration: build the AVQ of generation `gen`.  `first`: the
+// first compaction after a global relabel, which moved heights both ways, so
+// every vertex is scanned (and the candidate bitmap cleared); later ones use
+// the bitmap unless a gap must be applied (it lifts unmarked vertices too).
+template <int L>
+__device__ void build_avq(Ctx &c, bool phase1, int hcap, bool first)
 {
     const Params &P = c.P;
     const GraphDev &g = P.g;
@@ -1179,6 +1289,15 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap)
     if (phase1 && P.gap) {
         int cand = __ldcg(&P.st.ctl->gap_level[(gen + 2) % 3]);
         if (cand < n && __ldcg(P.st.count + cand) == 0) gap = cand;
+    }
+    if (P.st.touch) {
+        if (!first && gap == kUnvisited) {
+            build_avq_inc<L>(c, hcap);
+            return;
+        }
+        const long long nwords = ((long long)n + 31) >> 5;
+        for (long long w = (long long)c.bid * kBlock + threadIdx.x; w < nwords; w += (long long)c.nblk * kBlock)
+            __stcg(P.st.touch + w, 0u);
     }
     // kAvqVerts vertices per thread per step, their loads issued together
     // (heights, then excesses, then row offsets of the active ones).  The
@@ -1301,25 +1420,14 @@ __device__ __forceinline__ bool residual_to(const Params &P, long long slot, boo
     }
 }
 
-template <int L, int DIR>
-__device__ __forceinline__ void bfs_visit(Ctx &c, int v, int val, int nset, int n3)
+// Queue vertex v (row length d) in the next frontier, after its claim.
+template <int L>
+__device__ __forceinline__ void bfs_claimed(Ctx &c, int v, long long d, int nset, int n3)
 {
-    const Params &P = c.P;
-    bool fresh;
-    if (DIR == kBfsBackward) {
-        int *h = P.st.h;
-        fresh = __ldcg(h + v) == kUnvisited && atomicCAS(h + v, kUnvisited, val) == kUnvisited;
-    } else {
-        int *mark = P.st.count;
-        fresh = __ldcg(mark + v) == 0 && atomicCAS(mark + v, 0, val) == 0;
-    }
-    if (fresh) {
-        const long long d = degree<L>(P.g, v);
-        c.fe += d;
-        const int cls = classify(P, d);
-        if (cls == 2) hub_append(c, n3, nset, v, d, false, 0, kWChunk, hub_lead<L>(P.g, v));
-        else q_append(c, n3, nset, cls, v);
-    }
+    c.fe += d;
+    const int cls = classify(c.P, d);
+    if (cls == 2) hub_append(c, n3, nset, v, d, false, 0, kWChunk, hub_lead<L>(c.P.g, v));
+    else q_append(c, n3, nset, cls, v);
 }
 
 // Where the residual capacity that decides a BFS step over entry k of w's
@@ -1369,9 +1477,25 @@ __device__ __forceinline__ void bfs_entries(Ctx &c, int w, const long long (&k)[
         if (res[q]) open[q] = DIR == kBfsBackward ? __ldcg(P.st.h + v[q]) == kUnvisited
                                                   : __ldcg(P.st.count + v[q]) == 0;
     }
+    // Claims of the open entries: all compare-and-swaps first, then the row
+    // bounds of the vertices won, then the appends, so that a lane's claims
+    // overlap instead of waiting out three round trips each.
+    int old[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        old[q] = 1;
+        if (open[q]) old[q] = DIR == kBfsBackward ? atomicCAS(P.st.h + v[q], kUnvisited, val)
+                                                  : atomicCAS(P.st.count + v[q], 0, val);
+    }
+    long long d[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        d[q] = -1;
+        if (open[q] && old[q] == (DIR == kBfsBackward ? kUnvisited : 0)) d[q] = degree<L>(P.g, v[q]);
+    }
 #pragma unroll
     for (int q = 0; q < NB; ++q)
-        if (open[q]) bfs_visit<L, DIR>(c, v[q], val, nset, n3);
+        if (d[q] >= 0) bfs_claimed<L>(c, v[q], d[q], nset, n3);
 }
 
 // Scan frontier vertex w with `W` lanes starting at lane `sl`.
@@ -1447,6 +1571,7 @@ __device__ void bfs_level(Ctx &c, int val)
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
     long long scanned = 0;
     const int lane = threadIdx.x & 31;
+    const unsigned gwarp = c.bid * kWarps + (threadIdx.x >> 5);
     const unsigned nwarps = c.nblk * kWarps;
     {
         // warp-class rows (up to warp_max entries, of uneven length): taken
@@ -1455,7 +1580,7 @@ __device__ void bfs_level(Ctx &c, int val)
         const unsigned batch = c1 / (8u * nwarps) + 1u;
         unsigned next = 0, end = 0;
         for (;;) {
-            const unsigned i = grab_rows(&ctl->q_grab_w[s3], c1, batch, next, end);
+            const unsigned i = grab_rows(&ctl->q_grab_w[s3], c1, batch, next, end, gwarp, nwarps);
             if (i >= c1) break;
             const int w = __ldcg(q1 + i);
             bfs_row<L, DIR, 32>(c, w, lane, val, nset, n3);
@@ -1506,6 +1631,7 @@ __device__ void bfs_level(Ctx &c, int val)
 // ---------------------------------------------------------------------------
 constexpr int kBuThread = 32;
 constexpr int kBuStep = 4;
+constexpr long long kBuHubHead = 4 * 32 * kBuStep;  // hub-row entries a warp scans first
 
 // Over entry k of v's list (neighbour w returned): the residual capacity of
 // v -> w (backward BFS) or of w -> v (forward BFS; BCSR without the mirror:
@@ -1646,35 +1772,49 @@ __device__ void bfs_level_bu(Ctx &c, int val)
             }
         }
         __syncthreads();
-        // rows longer than kBuThread: one warp each
+        // Rows longer than kBuThread: one warp each.  Hub rows too, for their
+        // first kBuHubHead entries: the scan usually stops there (rows are
+        // sorted by neighbour id, and a renumbered graph puts the largest
+        // vertices, the likeliest parents, first), and a renumbered graph
+        // also puts whole runs of hubs into one block's vertex range, which
+        // one hub at a time on the whole block would take in turn.
         const unsigned nlo = c.sm.ndfr_lo, nhi = c.sm.ndfr_hi;
-        for (unsigned i = warp; i < nlo; i += kWarps) {
-            const int u = c.sm.dfr[i];
+        for (unsigned i = warp; i < nlo + nhi; i += kWarps) {
+            const bool hub = i >= nlo;
+            int *slot = hub ? &c.sm.dfr[span - 1 - (i - nlo)] : &c.sm.dfr[i];
+            const int u = *slot;
             const long long o = __ldg(g.off + u), dO = __ldg(g.off + u + 1) - o;
             long long ii = 0, d = dO;
             if (L == kRCSR) {
                 ii = __ldg(g.in_off + u);
                 d += __ldg(g.in_off + u + 1) - ii;
             }
-            for (long long r0 = 0; r0 < d; r0 += 32 * kBuStep) {
-                const bool h1 = bu_scan<L, DIR, 32, kBuStep>(P, u, o, dO, ii, d, r0, lane, want);
-                if (lane == 0) scanned += d - r0 < 32 * kBuStep ? d - r0 : 32 * kBuStep;
+            const long long lim = hub && d > kBuHubHead ? kBuHubHead : d;
+            bool found = false;
+            for (long long r0 = 0; r0 < lim; r0 += 32 * kBuStep) {
+                const bool h1 = bu_scan<L, DIR, 32, kBuStep>(P, u, o, dO, ii, lim, r0, lane, want);
+                if (lane == 0) scanned += lim - r0 < 32 * kBuStep ? lim - r0 : 32 * kBuStep;
                 if (__any_sync(kFull, h1)) {
                     if (lane == 0) bu_found<L, DIR>(c, u, d, val, nset, n3);
+                    found = true;
                     break;
                 }
             }
+            if (hub && lane == 0 && (found || lim == d)) *slot = -1;  // settled: no block scan
         }
-        // hub rows: the whole block, kBlock * kBuStep entries per step
+        __syncthreads();
+        // the rest of the hub rows not settled by their head: the whole block,
+        // kBlock * kBuStep entries per step
         for (unsigned i = 0; i < nhi; ++i) {
             const int u = c.sm.dfr[span - 1 - i];
+            if (u < 0) continue;  // block-uniform: read after the barrier above
             const long long o = __ldg(g.off + u), dO = __ldg(g.off + u + 1) - o;
             long long ii = 0, d = dO;
             if (L == kRCSR) {
                 ii = __ldg(g.in_off + u);
                 d += __ldg(g.in_off + u + 1) - ii;
             }
-            for (long long r0 = 0; r0 < d; r0 += (long long)kBlock * kBuStep) {
+            for (long long r0 = kBuHubHead; r0 < d; r0 += (long long)kBlock * kBuStep) {
                 const bool h1 = bu_scan<L, DIR, kBlock, kBuStep>(P, u, o, dO, ii, d, r0, threadIdx.x, want);
                 if (threadIdx.x == 0) scanned += d - r0 < kBlock * kBuStep ? d - r0 : kBlock * kBuStep;
                 if (__syncthreads_or(h1)) {
@@ -1967,7 +2107,7 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
             }
             continue;
         }
-        build_avq<L>(c, phase1, hcap);
+        build_avq<L>(c, phase1, hcap, i == 0);
         if (!grid_sync(c, 20)) return false;
         const unsigned tot = queue_total(P.st.ctl, c.gen);
         if (tot == 0) {

@@ -125,6 +125,10 @@ struct StateDev {
     long long *hub_rem[2];
     unsigned long long *hub_aux[2];
     unsigned *hub_done[2];
+    // one bit per vertex: pushed into, or left with excess by its owner,
+    // during the last push-relabel pass (candidates of the next AVQ); null =
+    // every AVQ compaction scans all vertices
+    unsigned *touch;
     Ctl *ctl;
     long long *bstats;          // [gridDim.x][kStatCount]
 };
