@@ -77,9 +77,13 @@ B_RESET = 20          # per slot per solve: cf0 4 + cf 4 + cfb 4 read, cf 4 + cf
 
 def algorithmic_bytes(st: dict, n: int, slots: int = 0) -> int:
     """Bytes the method must move in one solve launch, from the kernel's own
-    counters; `slots` adds the reset of the residual graph."""
+    counters; `slots` adds the reset of the residual graph.  An AVQ
+    compaction costs B_AVQ_SCAN per vertex when it scans every vertex, and
+    the candidate bitmap (n / 8 bytes) plus B_AVQ_SCAN per candidate when it
+    works from the bitmap."""
     return (B_ENTRY * st["arcs_scanned"] + B_ACTIVE * st["active_total"] +
-            B_AVQ_SCAN * n * st["iterations"] + B_PUSH * st["pushes"] +
+            B_AVQ_SCAN * n * st["avq_full_scans"] + (n // 8) * st["avq_bitmap_scans"] +
+            B_AVQ_SCAN * st["avq_candidates"] + B_PUSH * st["pushes"] +
             B_RELABEL * st["relabels"] + B_GR_ENTRY * st["gr_arcs_scanned"] +
             B_GR_VERTEX * n * st["global_relabels"] + B_RESET * slots)
 

@@ -160,6 +160,9 @@ typedef struct wbpr_stats {
     int64_t gaps;              /* gap-heuristic liftings applied */
     int64_t written_off;       /* excess written off by global relabels (§2.2) */
     double  solve_ms;          /* device time of the last wbpr_maxflow/_mincut solve */
+    int64_t avq_full_scans;    /* AVQ compactions that scanned every vertex */
+    int64_t avq_bitmap_scans;  /* AVQ compactions from the candidate bitmap (avq_incremental) */
+    int64_t avq_candidates;    /* marked vertices those compactions examined */
 } wbpr_stats;
 
 /* Sizes of a built handle. */
@@ -204,7 +207,11 @@ wbpr_graph *wbpr_build_ex(int64_t n, int64_t m, const int32_t *src, const int32_
  *              returns stranded excess to s so the flow is valid: 0 <= f <= cap,
  *              conservation at every vertex other than s and t.  Parallel arcs
  *              share their pair's flow greedily in input order; a self-loop
- *              gets 0.
+ *              gets 0.  A page-locked host buffer that is mapped into the
+ *              device's address space (pinned memory on a system with
+ *              unified addressing) is written directly by the kernel that
+ *              computes the flows; other host buffers are staged in device
+ *              memory and copied.
  * Re-solves from scratch on every call (idempotent).  Synchronises `stream`
  * before returning.
  */
@@ -230,7 +237,8 @@ wbpr_status wbpr_solve_status(wbpr_graph *g, wbpr_stream_t stream);
  *   source_side NULL, or n bytes (host or device pointer): 1 for the vertices
  *               reachable from s in the residual graph of a maximum flow (the
  *               smallest minimum-cut source side; the same for every maximum
- *               flow), else 0.
+ *               flow), else 0.  Mapped page-locked host buffers are
+ *               written directly, as for wbpr_maxflow's edge flows.
  * Reuses the state of a previous wbpr_maxflow with edge flows on this handle;
  * otherwise solves first.  Synchronises `stream`.
  */

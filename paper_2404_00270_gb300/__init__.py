@@ -79,7 +79,9 @@ class Stats(ctypes.Structure):
                 ("global_relabels", ctypes.c_int64), ("active_total", ctypes.c_int64),
                 ("arcs_scanned", ctypes.c_int64), ("gr_arcs_scanned", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("relabels", ctypes.c_int64), ("gaps", ctypes.c_int64),
-                ("written_off", ctypes.c_int64), ("solve_ms", ctypes.c_double)]
+                ("written_off", ctypes.c_int64), ("solve_ms", ctypes.c_double),
+                ("avq_full_scans", ctypes.c_int64), ("avq_bitmap_scans", ctypes.c_int64),
+                ("avq_candidates", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

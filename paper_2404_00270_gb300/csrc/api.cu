@@ -34,6 +34,21 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of a page-locked host buffer that kernels can write
+// directly (mapped into the device's address space), else null.  Outputs
+// in such buffers are written by the kernel that computes them, over the
+// host link, instead of being staged in device memory and copied.
+void *mapped_host_ptr(void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 }  // namespace
 
 wbpr_status set_error(wbpr_status st, const std::string &msg)
@@ -521,6 +536,9 @@ static wbpr_status collect(wbpr_graph *g, cudaStream_t st, bool accumulate)
         s.gr_arcs_scanned += x[kStatGrArcs];
         s.active_total += x[kStatActive];
         s.gaps += x[kStatGaps];
+        s.avq_full_scans += x[kStatAvqFull];
+        s.avq_bitmap_scans += x[kStatAvqInc];
+        s.avq_candidates += x[kStatAvqCand];
     }
     s.iterations = c.iterations;
     s.phase1_iterations = c.phase1_iterations;
@@ -565,8 +583,9 @@ wbpr_status wbpr_maxflow(wbpr_graph *g, wbpr_stream_t stream, int64_t *value, in
     if (rc != WBPR_OK) return rc;
     API_CUDA(cudaMemcpyAsync(g->pinned, g->e + g->t_int, sizeof(long long), cudaMemcpyDeviceToHost, st));
     if (want_flow) {
-        const bool dev = is_device_ptr(edge_flow);
-        int *out = edge_flow;
+        int *mapped = is_device_ptr(edge_flow) ? nullptr : (int *)mapped_host_ptr(edge_flow);
+        const bool dev = is_device_ptr(edge_flow) || mapped;
+        int *out = mapped ? mapped : edge_flow;
         if (!dev) {
             if (!g->edge_tmp) {
                 g->edge_tmp = (int *)g->alloc(sizeof(int) * (size_t)(g->m > 0 ? g->m : 1), st);
@@ -616,10 +635,12 @@ wbpr_status wbpr_mincut(wbpr_graph *g, wbpr_stream_t stream, int64_t *cut_value,
     int mode = kModeCut;
     if (!g->solved_flow) mode |= kModePreflow | kModePhase1 | kModePhase2;
     unsigned char *side = nullptr;
-    const bool dev = source_side && is_device_ptr(source_side);
+    unsigned char *mapped = source_side && !is_device_ptr(source_side)
+                                ? (unsigned char *)mapped_host_ptr(source_side) : nullptr;
+    const bool dev = source_side && (is_device_ptr(source_side) || mapped);
     if (source_side) {
         if (dev) {
-            side = source_side;
+            side = mapped ? mapped : source_side;
         } else {
             if (!g->side_tmp) {
                 g->side_tmp = (unsigned char *)g->alloc((size_t)g->n, st);

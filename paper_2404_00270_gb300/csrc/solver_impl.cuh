@@ -1233,6 +1233,7 @@ __device__ void build_avq_inc(Ctx &c, int hcap)
             if (lane >= o) incl += y;
         }
         const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (lane == 0 && total) atomicAdd((unsigned long long *)&c.sm.stats[kStatAvqCand], (u64)total);
         for (unsigned r0 = 0; r0 < total; r0 += 32) {
             const unsigned k = r0 + lane;  // this lane's candidate: the k-th marked vertex of the words
             unsigned src = 0;              // its word: lanes whose inclusive count is <= k
@@ -1271,6 +1272,7 @@ __device__ void build_avq_inc(Ctx &c, int hcap)
         }
     }
     if (nact) atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)nact);
+    if (c.bid == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&c.sm.stats[kStatAvqInc], 1ull);
 }
 
 // Step 1 of an iteration: build the AVQ of generation `gen`.  `first`: the
@@ -1299,6 +1301,7 @@ __device__ void build_avq(Ctx &c, bool phase1, int hcap, bool first)
         for (long long w = (long long)c.bid * kBlock + threadIdx.x; w < nwords; w += (long long)c.nblk * kBlock)
             __stcg(P.st.touch + w, 0u);
     }
+    if (c.bid == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&c.sm.stats[kStatAvqFull], 1ull);
     // kAvqVerts vertices per thread per step, their loads issued together
     // (heights, then excesses, then row offsets of the active ones).  The
     // blocks take the steps of kBlock * kAvqVerts vertices in turn, so that a

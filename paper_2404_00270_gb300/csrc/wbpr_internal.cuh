@@ -50,6 +50,9 @@ enum Stat : int {
     kStatGrArcs,
     kStatActive,
     kStatGaps,
+    kStatAvqFull,    // AVQ compactions that scanned every vertex
+    kStatAvqInc,     // AVQ compactions from the candidate bitmap
+    kStatAvqCand,    // candidates those examined
     kStatCount
 };
 

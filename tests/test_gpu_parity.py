@@ -131,7 +131,13 @@ def test_incremental_avq_same_results(layout, multi_push):
                                        (0, 1, 0, 1.5)]:
             o = m.wbpr_default_options()
             o.multi_push, o.avq_incremental, o.gap, o.cycle, o.gr_ratio = multi_push, inc, gap, cycle, ratio
-            check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o, ref=ref)
+            st = check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o, ref=ref)["stats"]
+            # every iteration compacts its AVQ one way or the other; a full
+            # scan follows every global relabel; no bitmap without the option
+            assert st["avq_full_scans"] + st["avq_bitmap_scans"] >= st["iterations"]
+            assert st["avq_full_scans"] >= 1
+            if not inc:
+                assert st["avq_bitmap_scans"] == 0 and st["avq_candidates"] == 0
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -239,6 +245,27 @@ def test_resolve_is_idempotent():
     assert a == b == c
     assert oracle.verify_flow(g.n, src, dst, cap, g.s, g.t, flow, c)[0] == 0
     G.close()
+
+
+def test_pinned_host_buffers_match_oracle():
+    """Inputs and outputs in page-locked host memory: the flows and the cut
+    side are written by the kernels straight into the mapped host buffers,
+    and equal the oracle's results (value, cut side, certified flow)."""
+    m = wb()
+    g = W.rmat(12, 16, 9)
+    src, dst, cap = g.numpy()
+    ref = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t)
+    hs, hd, hc = (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (src, dst, cap))
+    for layout in LAYOUTS:
+        G = m.wbpr_build(g.n, g.m, hs, hd, hc, g.s, g.t, layout_code(layout))
+        flow = torch.full((g.m,), -7, dtype=torch.int32).pin_memory()
+        side = torch.full((g.n,), 9, dtype=torch.uint8).pin_memory()
+        v = m.wbpr_maxflow(G, None, flow)
+        c = m.wbpr_mincut(G, None, side)
+        G.close()
+        assert v == c == ref["value"], layout
+        assert np.array_equal(side.numpy(), ref["source_side"]), layout
+        assert oracle.verify_flow(g.n, src, dst, cap, g.s, g.t, flow.numpy(), v)[0] == 0, layout
 
 
 def test_iteration_cap_reports_timeout_and_handle_survives():
