@@ -811,11 +811,22 @@ __device__ void mp_tile(Ctx &c, int u, int sl, bool phase1, int hcap)
 // Chunk ids are reserved in batches (one atomic on the generation's counter
 // per `WGrab::batch` chunks), so that hundreds of thousands of chunks per
 // pass do not all meet on one counter.
+// A warp's chunks come in runs of consecutive ids, which mostly belong to
+// one hub: the hub last looked up (queue position `lo`, chunk ids [s0, s1))
+// and its row (vertex u, BCSR/RCSR out row at ob of dout entries, RCSR in
+// row at ib of din entries) are kept, so that the next chunk of the same
+// hub costs no lookup.
 struct WGrab {
     unsigned next, end, batch;
-    __device__ WGrab(unsigned nchunks, unsigned nwarps) : next(0), end(0), batch(nchunks / (8u * nwarps) + 1u) {}
+    unsigned lo, s0, s1;
+    int u;
+    long long ob, dout, ib, din;
+    __device__ WGrab(unsigned nchunks, unsigned nwarps)
+        : next(0), end(0), batch(nchunks / (8u * nwarps) + 1u), lo(0), s0(0), s1(0), u(0), ob(0), dout(0), ib(0),
+          din(0) {}
 };
 
+template <int L>
 __device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks, WGrab &gb,
                                             unsigned &pos, unsigned &j, unsigned &nch)
 {
@@ -834,18 +845,29 @@ __device__ __forceinline__ bool grab_wchunk(Ctx &c, int s3, int set, unsigned nh
     }
     if (gb.next >= nchunks) return false;
     const unsigned id = gb.next++;
-    unsigned lo = 0, s0 = 0, s1 = 0;
-    if ((threadIdx.x & 31) == 0) {
-        {
+    if (!(id >= gb.s0 && id < gb.s1)) {  // another hub: look it up and load its row bounds
+        unsigned lo = 0, s0 = 0, s1 = 0;
+        if ((threadIdx.x & 31) == 0) {
             const unsigned *start = c.P.st.hub_start[set];
             lo = __ldcg(c.P.st.hub_chunk[set] + id);  // start[lo] <= id < start[lo + 1]
             s0 = __ldcg(start + lo);
             s1 = lo + 1 < nh ? __ldcg(start + lo + 1) : nchunks;
         }
+        gb.lo = __shfl_sync(kFull, lo, 0);
+        gb.s0 = __shfl_sync(kFull, s0, 0);
+        gb.s1 = __shfl_sync(kFull, s1, 0);
+        const GraphDev &g = c.P.g;
+        gb.u = __ldcg(c.P.st.q[set][2] + gb.lo);
+        gb.ob = __ldg(g.off + gb.u);
+        gb.dout = __ldg(g.off + gb.u + 1) - gb.ob;
+        if (L == kRCSR) {
+            gb.ib = __ldg(g.in_off + gb.u);
+            gb.din = __ldg(g.in_off + gb.u + 1) - gb.ib;
+        }
     }
-    pos = __shfl_sync(kFull, lo, 0);
-    j = id - __shfl_sync(kFull, s0, 0);
-    nch = __shfl_sync(kFull, s1, 0) - __shfl_sync(kFull, s0, 0);
+    pos = gb.lo;
+    j = id - gb.s0;
+    nch = gb.s1 - gb.s0;
     return true;
 }
 
@@ -910,18 +932,20 @@ __device__ __forceinline__ bool stage_wchunk(Ctx &c, int set, unsigned pos, unsi
 // the single push/relabel).
 template <int L>
 __device__ void pr_wchunk(Ctx &c, int set, unsigned pos, unsigned j, unsigned nch, bool phase1, int hcap,
-                          const int *staged = nullptr)
+                          const int *staged = nullptr, const WGrab *gb = nullptr)
 {
     constexpr int kPer = kWChunk / 32;
     const Params &P = c.P;
     const GraphDev &g = P.g;
     const int lane = threadIdx.x & 31;
-    const int u = __ldcg(P.st.q[set][2] + pos);
-    const long long ob = __ldg(g.off + u), dout = __ldg(g.off + u + 1) - ob;
+    // the hub and its row: from the grabber's cache (the chunk's own hub) or loaded
+    const int u = gb ? gb->u : __ldcg(P.st.q[set][2] + pos);
+    const long long ob = gb ? gb->ob : __ldg(g.off + u);
+    const long long dout = gb ? gb->dout : __ldg(g.off + u + 1) - ob;
     long long ib = 0, din = 0;
     if (L == kRCSR) {
-        ib = __ldg(g.in_off + u);
-        din = __ldg(g.in_off + u + 1) - ib;
+        ib = gb ? gb->ib : __ldg(g.in_off + u);
+        din = gb ? gb->din : __ldg(g.in_off + u + 1) - ib;
     }
     const long long deg = dout + din;
     const int lead = L == kBCSR ? (int)(ob & 3) : 0;
@@ -1119,13 +1143,13 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
                 // other buffer meanwhile.
                 int *wb = c.stage + (threadIdx.x >> 5) * kStageInts;
                 WGrab gb(nchunks, c.nblk * kWarps);
-                bool have = grab_wchunk(c, s3, set, nh, nchunks, gb, pos, j, nch);
+                bool have = grab_wchunk<L>(c, s3, set, nh, nchunks, gb, pos, j, nch);
                 bool st = have && stage_wchunk<L>(c, set, pos, j, wb);
                 cp_async_commit();
                 int b = 0;
                 while (have) {
                     unsigned pos2, j2, nch2;
-                    const bool have2 = grab_wchunk(c, s3, set, nh, nchunks, gb, pos2, j2, nch2);
+                    const bool have2 = grab_wchunk<L>(c, s3, set, nh, nchunks, gb, pos2, j2, nch2);
                     const bool st2 = have2 && stage_wchunk<L>(c, set, pos2, j2, wb + (b ^ 1) * 2 * kWChunk);
                     cp_async_commit();
                     cp_async_wait<1>();  // the current chunk's copies are done
@@ -1140,7 +1164,8 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
                 cp_async_wait<0>();
             } else {
                 WGrab gb(nchunks, c.nblk * kWarps);
-                while (grab_wchunk(c, s3, set, nh, nchunks, gb, pos, j, nch)) pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap);
+                while (grab_wchunk<L>(c, s3, set, nh, nchunks, gb, pos, j, nch))
+                    pr_wchunk<L>(c, set, pos, j, nch, phase1, hcap, nullptr, &gb);
             }
         }
     }
@@ -1533,17 +1558,16 @@ __device__ void bfs_row(Ctx &c, int w, int sl, int val, int nset, int n3)
 // all loads of a stage are issued together.  Returns the row entries of the
 // chunk on lane 0 (0 elsewhere).
 template <int L, int DIR>
-__device__ long long bfs_wchunk(Ctx &c, int set, unsigned pos, unsigned j, int val, int nset, int n3)
+__device__ long long bfs_wchunk(Ctx &c, const WGrab &gb, unsigned j, int val, int nset, int n3)
 {
     constexpr int NB = kWChunk / 32;
-    const GraphDev &g = c.P.g;
     const int lane = threadIdx.x & 31;
-    const int w = __ldcg(c.P.st.q[set][2] + pos);
-    const long long ob = __ldg(g.off + w), dout = __ldg(g.off + w + 1) - ob;
+    const int w = gb.u;  // the chunk's hub and its row, cached by the grabber
+    const long long ob = gb.ob, dout = gb.dout;
     long long ib = 0, din = 0;
     if (L == kRCSR) {
-        ib = __ldg(g.in_off + w);
-        din = __ldg(g.in_off + w + 1) - ib;
+        ib = gb.ib;
+        din = gb.din;
     }
     const long long deg = dout + din;
     const long long lo = (long long)j * kWChunk - (L == kBCSR ? (ob & 3) : 0);
@@ -1608,8 +1632,8 @@ __device__ void bfs_level(Ctx &c, int val)
         unsigned pos, j, nch;
         if (nchunks) {
             WGrab gb(nchunks, nwarps);
-            while (grab_wchunk(c, s3, set, nh, nchunks, gb, pos, j, nch))
-                scanned += bfs_wchunk<L, DIR>(c, set, pos, j, val, nset, n3);
+            while (grab_wchunk<L>(c, s3, set, nh, nchunks, gb, pos, j, nch))
+                scanned += bfs_wchunk<L, DIR>(c, gb, j, val, nset, n3);
         }
     }
     q_flush(c, n3, nset);
