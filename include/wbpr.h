@@ -143,8 +143,13 @@ typedef struct wbpr_options {
                                  from the vertices the last pass pushed into or left
                                  with excess (a bitmap the pushes mark); the first
                                  compaction after a global relabel, and one that
-                                 applies a gap, scan every vertex (default).  0 =
-                                 every compaction scans every vertex (Alg. 2). */
+                                 applies a gap, scan every vertex.  2 = as 1, and
+                                 while the AVQ stays small (at most 64 vertices per
+                                 block, no hub) every block compacts and processes
+                                 the marked vertices of its own bitmap words in the
+                                 same pass, saving a grid barrier per iteration
+                                 (default).  0 = every compaction scans every
+                                 vertex (Alg. 2). */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */

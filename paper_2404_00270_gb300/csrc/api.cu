@@ -121,7 +121,7 @@ void wbpr_default_options(wbpr_options *o)
     o->stage_hubs = 0;
     o->barrier_extra = 0;
     o->bottom_up_edges = 0;
-    o->avq_incremental = 1;
+    o->avq_incremental = 2;
 }
 
 wbpr_status wbpr_last_error(void) { return t_last; }
@@ -172,7 +172,7 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->barrier_extra < 0 || o->barrier_extra > 1024) return WBPR_EINVAL;
     if (o->stage_hubs != 0 && o->stage_hubs != 1) return WBPR_EINVAL;
     if (o->bottom_up_edges != 0 && o->bottom_up_edges != 1) return WBPR_EINVAL;
-    if (o->avq_incremental != 0 && o->avq_incremental != 1) return WBPR_EINVAL;
+    if (o->avq_incremental < 0 || o->avq_incremental > 2) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -457,6 +457,7 @@ Params make_params(wbpr_graph *g, int mode)
     }
     // (the thread-centric baseline builds no AVQ: its pushes mark nothing)
     p.st.touch = (g->opts.avq_incremental && !g->opts.thread_centric) ? g->touch : nullptr;
+    p.local_passes = g->opts.avq_incremental >= 2 ? 1 : 0;
     p.st.ctl = g->ctl;
     p.st.bstats = g->bstats;
     p.mode = mode;

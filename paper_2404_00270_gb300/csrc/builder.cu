@@ -84,18 +84,22 @@ struct InVal {
 };
 
 // Keys and values of the head-side sort from the (u, v)-sorted arcs k < mp
-// (self-loops sorted after them).  Also flags (dup = 1) a parallel arc: two
+// (self-loops sorted after them), and the capacities in that order (ctail,
+// so that the merge reads the tail side's capacities in sequence instead of
+// gathering them a second time).  Also flags (dup = 1) a parallel arc: two
 // equal neighbouring keys, the only case that needs the duplicate prefix.
 __global__ void in_prep(long long mp, int b, const u64 *key, const unsigned *val, const int *cap, unsigned *kin,
-                        InVal *vin, int *dup)
+                        InVal *vin, int *ctail, int *dup)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const u64 mask = (1ull << b) - 1;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < mp; k += stride) {
         const u64 x = key[k];
         const unsigned i = val[k];
+        const int c = cap[i];
         kin[k] = (unsigned)(x & mask);
-        vin[k] = InVal{(unsigned)(x >> b), i, cap[i]};
+        vin[k] = InVal{(unsigned)(x >> b), i, c};
+        ctail[k] = c;
         if (k > 0 && key[k - 1] == x) *dup = 1;
     }
 }
@@ -115,15 +119,14 @@ struct HalfLess {
     }
 };
 
-// k-th tail-side half-entry.
+// k-th tail-side half-entry (ctail: capacities in the (u, v) order).
 struct OutHalf {
     const u64 *key;
     const unsigned *val;
-    const int *cap;
+    const int *ctail;
     __host__ __device__ HalfRec operator()(long long k) const
     {
-        const unsigned i = val[k];
-        return HalfRec{key[k], 2u * i, cap[i]};
+        return HalfRec{key[k], 2u * val[k], ctail[k]};
     }
 };
 
@@ -635,10 +638,12 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_ALLOC(kinb, unsigned, mp, pool);
         BUILD_ALLOC(vin, InVal, mp, pool);
         BUILD_ALLOC(vinb, InVal, mp, pool);
+        int *ctail = nullptr;
+        BUILD_ALLOC(ctail, int, mp, pool);
         cub::DoubleBuffer<unsigned> dki(kin, kinb);
         cub::DoubleBuffer<InVal> dvi(vin, vinb);
         if (mp > 0) {
-            in_prep<<<grid_for(mp), 256, 0, st>>>(mp, kb, kos, vos, cap, kin, vin, dup);
+            in_prep<<<grid_for(mp), 256, 0, st>>>(mp, kb, kos, vos, cap, kin, vin, ctail, dup);
             BUILD_CUDA(cudaGetLastError());
             size_t nb = 0;
             BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dki, dvi, (int64_t)mp, 0, kb, st));
@@ -664,7 +669,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         BUILD_ALLOC(v2s, unsigned, len, pool);
         BUILD_ALLOC(cj, int, len, pool);
         if (len > 0) {
-            auto in1 = thrust::make_transform_iterator(thrust::counting_iterator<long long>(0), OutHalf{kos, vos, cap});
+            auto in1 = thrust::make_transform_iterator(thrust::counting_iterator<long long>(0), OutHalf{kos, vos, ctail});
             auto in2 = thrust::make_transform_iterator(thrust::counting_iterator<long long>(0), InHalf{kb, kis, vis});
             auto out = thrust::make_transform_output_iterator(thrust::make_zip_iterator(k2s, v2s, cj), SplitHalf{});
             size_t nb = 0;
@@ -679,6 +684,7 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         pool.release(vis);
         pool.release(kos);
         pool.release(vos);
+        pool.release(ctail);
 
         // ---- duplicate prefix (edge-flow split in input order) ------------------
         // The tail-side half-entries of duplicates of (u, v) sit in input order

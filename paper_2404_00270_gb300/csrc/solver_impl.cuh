@@ -274,6 +274,17 @@ __device__ __forceinline__ void reset_rotating(Ctx &c, int gen)
     }
 }
 
+// The counters of a block-local pass of generation gen live in slot gen % 3;
+// every push-relabel pass of generation gen clears slot (gen + 1) % 3 for
+// the next one (its last readers passed the barrier before this pass).
+__device__ __forceinline__ void reset_local_slot(Ctx &c, int gen)
+{
+    if (c.bid == 0 && threadIdx.x == 0) {
+        c.P.st.ctl->local_active[(gen + 1) % 3] = 0;
+        c.P.st.ctl->local_defer[(gen + 1) % 3] = 0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Hub class: a vertex whose residual list is longer than warp_max is split
 // into chunks: of kWChunk entries for a push-relabel pass (one warp each),
@@ -1098,6 +1109,7 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
     const int gen = c.gen, s3 = gen % 3, set = gen & 1;
     const u64 wt0 = warp_clock(P);
     reset_rotating(c, gen);
+    reset_local_slot(c, gen);
     const unsigned c0 = __ldcg(&ctl->q_count[s3][0]);
     const unsigned c1 = __ldcg(&ctl->q_count[s3][1]);
     const int lane = threadIdx.x & 31;
@@ -1169,6 +1181,98 @@ __device__ void pr_process(Ctx &c, bool phase1, int hcap)
             }
         }
     }
+    warp_clock_add(c, wt0);
+}
+
+// Block-local pass for a small AVQ (avq_incremental = 2): every block takes
+// the candidate-bitmap words w = bid, bid + nblk, ... (so that a run of
+// consecutive vertices spreads over the blocks), clears them atomically,
+// ranks the marked vertices that are active by tile class in shared memory
+// and processes them itself: the compaction and the pass share one grid
+// barrier.  Every vertex belongs to one word and every word to one block,
+// so a vertex is processed at most once per pass, by its word's block.  A
+// push may land in a word already cleared in this pass (its target waits
+// for the next pass), or in one not yet cleared (its target may be
+// processed in this pass, with the excess that has arrived).  Hubs, and
+// candidates beyond the block's staging, stay marked and make the next
+// iteration a full one.  The team's active count and the deferral flag go
+// to ctl->local_active / local_defer, slot gen % 3.
+template <int L, int SW>
+__device__ void pr_local(Ctx &c, bool phase1, int hcap)
+{
+    const Params &P = c.P;
+    const GraphDev &g = P.g;
+    const int s = g.s, t = g.t;
+    const int gen = c.gen, s3 = gen % 3;
+    const u64 wt0 = warp_clock(P);
+    reset_local_slot(c, gen);  // (the rotating queue counters are cleared after the pass: see iterate())
+    const long long nwords = ((long long)g.n + 31) >> 5;
+    int *cand = c.sm.qbuf[0];
+    int *smallq = c.sm.qbuf[1];
+    int *warpq = c.sm.qbuf[2];
+    __syncthreads();  // qcnt is zero between passes; every thread sees it before the counts grow
+    bool defer = false;
+    long long nc = 0;
+    for (long long w = c.bid + (long long)threadIdx.x * c.nblk; w < nwords; w += (long long)kBlock * c.nblk) {
+        unsigned bits = __ldcg(P.st.touch + w);
+        if (!bits) continue;
+        bits = atomicExch(P.st.touch + w, 0u);
+        while (bits) {
+            const unsigned pos = atomicAdd(&c.sm.qcnt[0], 1u);
+            if (pos >= (unsigned)kQueueCap) {  // staging full: leave the rest marked
+                atomicOr(P.st.touch + w, bits);
+                defer = true;
+                break;
+            }
+            cand[pos] = (int)(w * 32 + (__ffs(bits) - 1));
+            bits &= bits - 1;
+            ++nc;
+        }
+    }
+    __syncthreads();
+    const unsigned ncand = c.sm.qcnt[0] < (unsigned)kQueueCap ? c.sm.qcnt[0] : (unsigned)kQueueCap;
+    long long nact = 0;
+    for (unsigned j = threadIdx.x; j < ncand; j += kBlock) {
+        const int v = cand[j];
+        if (v == s || v == t || __ldcg(P.st.h + v) >= hcap || __ldcg(P.st.e + v) <= 0) continue;
+        const int cls = classify(P, degree<L>(g, v));
+        if (cls == 2) {  // a hub: chunked over the whole team by a full pass
+            atomicOr(P.st.touch + (v >> 5), 1u << (v & 31));
+            defer = true;
+            continue;
+        }
+        ++nact;
+        if (cls == 0) smallq[atomicAdd(&c.sm.qcnt[1], 1u)] = v;
+        else warpq[atomicAdd(&c.sm.qcnt[2], 1u)] = v;
+    }
+    __syncthreads();
+    const unsigned nsmall = c.sm.qcnt[1], nwarp = c.sm.qcnt[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (unsigned i = warp; i < nwarp; i += kWarps) {
+        if (P.multi_push) mp_tile<L, 32>(c, warpq[i], lane, phase1, hcap);
+        else pr_tile<L, 32>(c, warpq[i], lane, phase1, hcap);
+    }
+    constexpr unsigned TPW = 32 / SW;
+    for (unsigned base = warp * TPW; base < nsmall; base += kWarps * TPW) {
+        const unsigned idx = base + lane / SW;
+        const int u = idx < nsmall ? smallq[idx] : -1;
+        if (P.multi_push) mp_tile<L, SW>(c, u, lane % SW, phase1, hcap);
+        else pr_tile<L, SW>(c, u, lane % SW, phase1, hcap);
+    }
+    const long long ba = block_sum(c, nact);
+    const long long bc = block_sum(c, nc);
+    const int bd = __syncthreads_or(defer);
+    if (threadIdx.x == 0) {
+        if (ba) {
+            atomicAdd(&P.st.ctl->local_active[s3], (unsigned)ba);
+            atomicAdd((unsigned long long *)&c.sm.stats[kStatActive], (u64)ba);
+        }
+        if (bc) atomicAdd((unsigned long long *)&c.sm.stats[kStatAvqCand], (u64)bc);
+        if (bd) atomicExch(&P.st.ctl->local_defer[s3], 1);
+        if (c.bid == 0) atomicAdd((unsigned long long *)&c.sm.stats[kStatAvqInc], 1ull);
+    }
+    if (threadIdx.x < kClasses) c.sm.qcnt[threadIdx.x] = 0;
+    __syncthreads();
     warp_clock_add(c, wt0);
 }
 
@@ -2107,6 +2211,11 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
 {
     const Params &P = c.P;
     const int hcap = phase1 ? P.g.n : 2 * P.g.n;
+    // avq_incremental = 2: after a pass whose AVQ held at most 64 vertices
+    // per block and no hub (or a block-local pass that processed that few
+    // and deferred nothing), the next pass runs block-locally (pr_local).
+    const unsigned local_max = 64u * c.nblk;
+    bool local = false;
     for (long long i = 0; i < max_it; ++i) {
         // Time-balanced global relabel: once the iterations since the last
         // global relabel have taken gr_ratio times as long as it did.
@@ -2134,22 +2243,43 @@ __device__ bool iterate(Ctx &c, bool phase1, long long max_it, long long *it_tot
             }
             continue;
         }
-        build_avq<L>(c, phase1, hcap, i == 0);
-        if (!grid_sync(c, 20)) return false;
-        const unsigned tot = queue_total(P.st.ctl, c.gen);
-        if (tot == 0) {
-            reset_rotating(c, c.gen);
-            if (!grid_sync(c, 21)) return false;
+        if (local && phase1 && P.gap) {  // a pending gap needs a full compaction
+            const int cand = __ldcg(&P.st.ctl->gap_level[(c.gen + 2) % 3]);
+            if (cand < P.g.n && __ldcg(P.st.count + cand) == 0) local = false;
+        }
+        if (local) {
+            pr_local<L, SW>(c, phase1, hcap);
+            if (c.bid == 0 && threadIdx.x == 0 && P.gr_ratio > 0.f) {
+                const u64 now = global_ns();
+                if ((float)(now - c.gr_end_ns) >= P.gr_ratio * (float)c.gr_ns) P.st.ctl->gr_due_gen = c.gen;
+            }
+            if (!grid_sync(c, 24)) return false;
+            const unsigned na = __ldcg(&P.st.ctl->local_active[c.gen % 3]);
+            const bool deferred = __ldcg(&P.st.ctl->local_defer[c.gen % 3]) != 0;
+            reset_rotating(c, c.gen);  // every block has read generation gen - 1's gap candidate
             c.gen++;
-            break;
+            if (na == 0 && !deferred) break;  // no vertex was active: as an empty AVQ
+            local = !deferred && na <= local_max;
+        } else {
+            build_avq<L>(c, phase1, hcap, i == 0);
+            if (!grid_sync(c, 20)) return false;
+            const unsigned tot = queue_total(P.st.ctl, c.gen);
+            const bool hubs = (__ldcg(&P.st.ctl->hub_pack[c.gen % 3]) >> 40) != 0;
+            if (tot == 0) {
+                reset_rotating(c, c.gen);
+                if (!grid_sync(c, 21)) return false;
+                c.gen++;
+                break;
+            }
+            pr_process<L, SW>(c, phase1, hcap);
+            if (c.bid == 0 && threadIdx.x == 0 && P.gr_ratio > 0.f) {
+                const u64 now = global_ns();
+                if ((float)(now - c.gr_end_ns) >= P.gr_ratio * (float)c.gr_ns) P.st.ctl->gr_due_gen = c.gen;
+            }
+            if (!grid_sync(c, 22)) return false;
+            c.gen++;
+            local = P.local_passes && P.st.touch && !hubs && tot <= local_max;
         }
-        pr_process<L, SW>(c, phase1, hcap);
-        if (c.bid == 0 && threadIdx.x == 0 && P.gr_ratio > 0.f) {
-            const u64 now = global_ns();
-            if ((float)(now - c.gr_end_ns) >= P.gr_ratio * (float)c.gr_ns) P.st.ctl->gr_due_gen = c.gen;
-        }
-        if (!grid_sync(c, 22)) return false;
-        c.gen++;
         ++*it_total;
         if (*it_total >= P.max_iterations) {
             if (c.bid == 0 && threadIdx.x == 0) {

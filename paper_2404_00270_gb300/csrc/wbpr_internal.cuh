@@ -83,6 +83,8 @@ struct __align__(128) Ctl {
     long long dead_count;    // vertices marked unreachable (dead[]) in the current phase
     long long dead_edges;    // their residual-list entries
     long long fedges[3];     // residual-list entries of the BFS frontier, by generation % 3
+    unsigned local_active[3];  // block-local passes: active vertices processed, by generation % 3
+    int local_defer[3];        // block-local passes: candidates left marked for a full pass
 };
 
 struct GraphDev {
@@ -172,6 +174,7 @@ struct Params {
     int thread_centric;          // 1: thread-centric iterations (one thread per vertex, no AVQ)
     unsigned long long *warp_ns; // optional: per warp of the grid, device ns spent in push-relabel passes
     int barrier_extra;           // tests: arrivals a grid barrier waits for beyond the grid
+    int local_passes;            // 1: small AVQs are compacted and processed block by block (with touch)
 };
 
 // Persistent server (solver.cu).  The rings, results, published counts and

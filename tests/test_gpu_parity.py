@@ -118,17 +118,18 @@ def test_option_sweep_same_results(multi_push):
 @pytest.mark.parametrize("multi_push", [1, 0])
 def test_incremental_avq_same_results(layout, multi_push):
     """AVQ compactions built from the candidate bitmap between global
-    relabels (avq_incremental = 1, the default) and full scans of every
-    vertex (0) both give the oracle's value, cut side and a certified flow,
-    with the gap heuristic on and off and with short and long relabel
-    cycles (many incremental compactions in a row)."""
+    relabels (avq_incremental = 1), block-local passes for small AVQs on top
+    of that (2, the default) and full scans of every vertex (0) all give the
+    oracle's value, cut side and a certified flow, with the gap heuristic on
+    and off and with short and long relabel cycles (many incremental
+    compactions and local passes in a row)."""
     m = wb()
     graphs = [W.rmat(12, 16, 5), W.grid(40, 40, 3), W.random_small(300, 3000, 77, cap_lo=0, cap_hi=50)]
     for g in graphs:
         src, dst, cap = g.numpy()
         ref = oracle.maxflow_pr(g.n, src, dst, cap, g.s, g.t)
-        for inc, gap, cycle, ratio in [(1, 1, 0, 1.5), (1, 0, 0, 1.5), (1, 1, 1000, 0.0), (1, 0, 50, 0.0),
-                                       (0, 1, 0, 1.5)]:
+        for inc, gap, cycle, ratio in [(2, 1, 0, 1.5), (2, 0, 0, 1.5), (2, 1, 1000, 0.0), (2, 0, 50, 0.0),
+                                       (1, 1, 0, 1.5), (1, 0, 1000, 0.0), (0, 1, 0, 1.5)]:
             o = m.wbpr_default_options()
             o.multi_push, o.avq_incremental, o.gap, o.cycle, o.gr_ratio = multi_push, inc, gap, cycle, ratio
             st = check_against_oracle(g.n, src, dst, cap, g.s, g.t, layout, o, ref=ref)["stats"]
