@@ -138,7 +138,9 @@ typedef struct wbpr_options {
     int32_t bottom_up_edges;  /* BFS direction rule: 1 = compare the residual-list
                                  entries of the frontier, times bottom_up, with
                                  those of the vertices not yet visited; 0 = compare
-                                 vertex counts (default) */
+                                 vertex counts (default); 2 = entries in the global
+                                 relabels of phase 1 and in the cut, vertex counts
+                                 in the global relabels of phase 2 */
     int32_t avq_incremental;  /* 1 = between two global relabels, build the AVQ only
                                  from the vertices the last pass pushed into or left
                                  with excess (a bitmap the pushes mark); the first
@@ -150,6 +152,12 @@ typedef struct wbpr_options {
                                  same pass, saving a grid barrier per iteration
                                  (default).  0 = every compaction scans every
                                  vertex (Alg. 2). */
+    int32_t lean_build;       /* build time: 1 = every block the builder launches fits
+                                 beside two blocks of a resident server kernel per SM
+                                 (radix sorts with 256-thread blocks, duplicate-arc
+                                 prefixes by run; never renumbers), for builds that
+                                 run while wbpr_server_start's kernel is resident.
+                                 0 = CUB's own tuning (default, faster alone). */
 } wbpr_options;
 
 /* Counters of the last solve on a handle. */
@@ -422,6 +430,12 @@ typedef struct wbpr_server_options {
     int32_t small_blocks;  /* single-block teams */
     int32_t idle_ms;       /* the kernel stops after this long without requests */
     int64_t big_slots;     /* class boundary in residual slots */
+    int32_t build_room;    /* 1 = the server kernel asks for the largest shared-memory
+                              carveout, so that the blocks of builds that run while it
+                              is resident (lean builds, wbpr_options.lean_build) find
+                              shared memory beside two server blocks per SM (default);
+                              0 = the default carveout (more L1; nothing is built
+                              while the server runs) */
 } wbpr_server_options;
 void wbpr_server_default_options(wbpr_server_options *opts);
 wbpr_server *wbpr_server_start(const wbpr_server_options *opts);

@@ -68,7 +68,7 @@ class Options(ctypes.Structure):
                 ("renumber", ctypes.c_int32), ("thread_centric", ctypes.c_int32),
                 ("warp_time", ctypes.c_int32), ("stage_hubs", ctypes.c_int32),
                 ("barrier_extra", ctypes.c_int32), ("bottom_up_edges", ctypes.c_int32),
-                ("avq_incremental", ctypes.c_int32)]
+                ("avq_incremental", ctypes.c_int32), ("lean_build", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -395,7 +395,7 @@ def wbpr_maxflow_bcsr_noalloc(n, slots, s, t, off, col, cap, rev, stream=None, d
 class ServerOptions(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("capacity", ctypes.c_int32), ("team_blocks", ctypes.c_int32),
                 ("big_teams", ctypes.c_int32), ("small_blocks", ctypes.c_int32), ("idle_ms", ctypes.c_int32),
-                ("big_slots", ctypes.c_int64)]
+                ("big_slots", ctypes.c_int64), ("build_room", ctypes.c_int32)]
 
 
 def wbpr_server_default_options() -> ServerOptions:

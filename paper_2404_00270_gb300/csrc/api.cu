@@ -171,8 +171,9 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->warp_time != 0 && o->warp_time != 1) return WBPR_EINVAL;
     if (o->barrier_extra < 0 || o->barrier_extra > 1024) return WBPR_EINVAL;
     if (o->stage_hubs != 0 && o->stage_hubs != 1) return WBPR_EINVAL;
-    if (o->bottom_up_edges != 0 && o->bottom_up_edges != 1) return WBPR_EINVAL;
+    if (o->bottom_up_edges < 0 || o->bottom_up_edges > 2) return WBPR_EINVAL;
     if (o->avq_incremental < 0 || o->avq_incremental > 2) return WBPR_EINVAL;
+    if (o->lean_build != 0 && o->lean_build != 1) return WBPR_EINVAL;
     return WBPR_OK;
 }
 
@@ -267,7 +268,9 @@ wbpr_graph *wbpr_build_ex(int64_t n, int64_t m, const int32_t *src, const int32_
     g->t = t;
     g->layout = layout;
     g->opts = o;
-    g->renumbered = o.renumber == 1 || (o.renumber == -1 && n >= kRenumberAutoVertices);
+    g->lean = o.lean_build != 0;
+    // (a lean build never renumbers: the renumbering sort runs on CUB's own tuning)
+    g->renumbered = !g->lean && (o.renumber == 1 || (o.renumber == -1 && n >= kRenumberAutoVertices));
     memset(&g->stats, 0, sizeof(g->stats));
     auto fail = [&](wbpr_status code, const std::string &msg) -> wbpr_graph * {
         wbpr_status keep = t_last == WBPR_OK ? code : t_last;

@@ -36,6 +36,60 @@ namespace {
 
 typedef unsigned long long u64;
 
+// A CUB radix-sort tuning for builds that run while a persistent server
+// kernel holds two blocks of every SM (wbpr_options.lean_build): onesweep
+// and single-tile blocks of 256 threads with few items per thread, so that
+// a sort block fits in the registers and shared memory the server leaves.
+// CUB's own tuning for this GPU uses 384-thread onesweep blocks of up to 96
+// registers a thread (u64 keys), more than half an SM's register file.
+template <typename KeyT, typename ValueT, typename OffsetT>
+struct LeanRadixHub {
+    using DominantT = ::cuda::std::_If<(sizeof(ValueT) > sizeof(KeyT)), ValueT, KeyT>;
+    struct Policy : cub::ChainedPolicy<1000, Policy, Policy> {
+        static constexpr bool ONESWEEP = true;
+        static constexpr int ONESWEEP_RADIX_BITS = 8;
+        using HistogramPolicy = cub::AgentRadixSortHistogramPolicy<128, 8, 1, KeyT, ONESWEEP_RADIX_BITS>;
+        using ExclusiveSumPolicy = cub::AgentRadixSortExclusiveSumPolicy<256, ONESWEEP_RADIX_BITS>;
+        using OnesweepPolicy =
+            cub::AgentRadixSortOnesweepPolicy<256, 12, DominantT, 1, cub::RADIX_RANK_MATCH_EARLY_COUNTS_ANY,
+                                              cub::BLOCK_SCAN_RAKING_MEMOIZE, cub::RADIX_SORT_STORE_DIRECT,
+                                              ONESWEEP_RADIX_BITS>;
+        using ScanPolicy = cub::AgentScanPolicy<256, 8, OffsetT, cub::BLOCK_LOAD_WARP_TRANSPOSE, cub::LOAD_DEFAULT,
+                                                cub::BLOCK_STORE_WARP_TRANSPOSE, cub::BLOCK_SCAN_RAKING_MEMOIZE>;
+        using DownsweepPolicy =
+            cub::AgentRadixSortDownsweepPolicy<256, 8, DominantT, cub::BLOCK_LOAD_TRANSPOSE, cub::LOAD_DEFAULT,
+                                               cub::RADIX_RANK_MATCH, cub::BLOCK_SCAN_WARP_SCANS, 6>;
+        using AltDownsweepPolicy =
+            cub::AgentRadixSortDownsweepPolicy<256, 8, DominantT, cub::BLOCK_LOAD_TRANSPOSE, cub::LOAD_DEFAULT,
+                                               cub::RADIX_RANK_MEMOIZE, cub::BLOCK_SCAN_WARP_SCANS, 5>;
+        using UpsweepPolicy = cub::AgentRadixSortUpsweepPolicy<256, 8, DominantT, cub::LOAD_DEFAULT, 6>;
+        using AltUpsweepPolicy = cub::AgentRadixSortUpsweepPolicy<256, 8, DominantT, cub::LOAD_DEFAULT, 5>;
+        using SingleTilePolicy =
+            cub::AgentRadixSortDownsweepPolicy<256, 8, DominantT, cub::BLOCK_LOAD_DIRECT, cub::LOAD_LDG,
+                                               cub::RADIX_RANK_MEMOIZE, cub::BLOCK_SCAN_WARP_SCANS, 6>;
+        using SegmentedPolicy =
+            cub::AgentRadixSortDownsweepPolicy<256, 8, DominantT, cub::BLOCK_LOAD_TRANSPOSE, cub::LOAD_DEFAULT,
+                                               cub::RADIX_RANK_MEMOIZE, cub::BLOCK_SCAN_WARP_SCANS, 6>;
+        using AltSegmentedPolicy =
+            cub::AgentRadixSortDownsweepPolicy<256, 8, DominantT, cub::BLOCK_LOAD_TRANSPOSE, cub::LOAD_DEFAULT,
+                                               cub::RADIX_RANK_MEMOIZE, cub::BLOCK_SCAN_WARP_SCANS, 5>;
+    };
+    using MaxPolicy = Policy;
+};
+
+// Stable ascending radix sort of key/value pairs over bits [b0, b1), with
+// CUB's tuning or, for lean builds, LeanRadixHub's.
+template <typename K, typename V>
+cudaError_t sort_pairs(bool lean, void *tmp, size_t &bytes, cub::DoubleBuffer<K> &k, cub::DoubleBuffer<V> &v,
+                       int64_t n, int b0, int b1, cudaStream_t st)
+{
+    if (!lean) return cub::DeviceRadixSort::SortPairs(tmp, bytes, k, v, n, b0, b1, st);
+    using OffsetT = cub::detail::choose_offset_t<int64_t>;  // the offset type CUB's own entry point picks
+    using D = cub::DispatchRadixSort<cub::SortOrder::Ascending, K, V, OffsetT, cub::detail::identity_decomposer_t,
+                                     LeanRadixHub<K, V, OffsetT>>;
+    return D::Dispatch(tmp, bytes, k, v, (OffsetT)n, b0, b1, true, st);
+}
+
 // Arc keys (u << b) | v, self-loops the all-ones key, values the input
 // index; ids are checked before use (flag 1: out of range or negative
 // capacity).  With perm (a renumbered handle) the key holds the new ids
@@ -153,6 +207,24 @@ struct SplitHalf {
 struct TailPart {
     __host__ __device__ int operator()(int x) const { return x > 0 ? x : 0; }
 };
+
+// Lean builds: the duplicate prefix by walking each run of equal keys from
+// its head (runs are as long as the duplicates of one pair).
+__global__ void run_prefix(long long len, const u64 *key, const unsigned *pos, const int *cj, int *prefix)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len; j += stride) {
+        const u64 k = key[j];
+        if (j > 0 && key[j - 1] == k) continue;
+        long long acc = 0;  // (a pair whose capacities exceed INT32_MAX fails the build when merged)
+        for (long long i = j; i < len && key[i] == k; ++i) {
+            const int x = cj[i];
+            if (x < 0) continue;  // head-side half-entry
+            prefix[pos[i] >> 1] = (int)acc;
+            acc += x;
+        }
+    }
+}
 
 __global__ void scatter_prefix(long long len, const unsigned *pos, const int *pre, int *prefix)
 {
@@ -615,10 +687,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         cub::DoubleBuffer<unsigned> dvo(vo, vob);
         if (m > 0) {
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dko, dvo, (int64_t)m, 0, end_bit, st));
+            BUILD_CUDA(sort_pairs(g->lean, nullptr, nb, dko, dvo, (int64_t)m, 0, end_bit, st));
             void *t3 = pool.get(nb);
             if (!t3) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t3, nb, dko, dvo, (int64_t)m, 0, end_bit, st));
+            BUILD_CUDA(sort_pairs(g->lean, t3, nb, dko, dvo, (int64_t)m, 0, end_bit, st));
             pool.release(t3);
         }
         u64 *kos = dko.Current();
@@ -646,10 +718,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             in_prep<<<grid_for(mp), 256, 0, st>>>(mp, kb, kos, vos, cap, kin, vin, ctail, dup);
             BUILD_CUDA(cudaGetLastError());
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dki, dvi, (int64_t)mp, 0, kb, st));
+            BUILD_CUDA(sort_pairs(g->lean, nullptr, nb, dki, dvi, (int64_t)mp, 0, kb, st));
             void *t6 = pool.get(nb);
             if (!t6) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t6, nb, dki, dvi, (int64_t)mp, 0, kb, st));
+            BUILD_CUDA(sort_pairs(g->lean, t6, nb, dki, dvi, (int64_t)mp, 0, kb, st));
             pool.release(t6);
         }
         unsigned *kis = dki.Current();
@@ -710,7 +782,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             int h_dup = 0;
             BUILD_CUDA(cudaMemcpyAsync(&h_dup, dup, sizeof(int), cudaMemcpyDeviceToHost, st));
             BUILD_CUDA(cudaStreamSynchronize(st));
-            if (h_dup) {
+            if (h_dup && g->lean) {
+                run_prefix<<<grid_for(len), 256, 0, st>>>(len, k2s, v2s, cj, g->prefix);
+                BUILD_CUDA(cudaGetLastError());
+            } else if (h_dup) {
                 // parallel arcs: each one's prefix (capacity of its earlier duplicates)
                 int *pre;
                 BUILD_ALLOC(pre, int, len, pool);
@@ -788,10 +863,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
         cub::DoubleBuffer<unsigned> dv(val1, val1b);
         if (m > 0) {
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dk, dv, (int64_t)m, 0, end_bit, st));
+            BUILD_CUDA(sort_pairs(g->lean, nullptr, nb, dk, dv, (int64_t)m, 0, end_bit, st));
             void *t1 = pool.get(nb);
             if (!t1) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t1, nb, dk, dv, (int64_t)m, 0, end_bit, st));
+            BUILD_CUDA(sort_pairs(g->lean, t1, nb, dk, dv, (int64_t)m, 0, end_bit, st));
             pool.release(t1);
         }
         u64 *ks = dk.Current();
@@ -824,10 +899,10 @@ wbpr_status build_graph(wbpr_graph *g, const int *src, const int *dst, const int
             cub::DoubleBuffer<u64> dki(kin, kinb);
             cub::DoubleBuffer<unsigned> dvi(vin, vinb);
             size_t nb = 0;
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
+            BUILD_CUDA(sort_pairs(g->lean, nullptr, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
             void *t5 = pool.get(nb);
             if (!t5) return set_error(WBPR_ENOMEM, "build: device allocation failed");
-            BUILD_CUDA(cub::DeviceRadixSort::SortPairs(t5, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
+            BUILD_CUDA(sort_pairs(g->lean, t5, nb, dki, dvi, (int64_t)mp, 0, end_bit, st));
             pool.release(t5);
             rcsr_in<<<grid_for(mp), 256, 0, st>>>(mp, kb, dki.Current(), dvi.Current(), g->in_col, g->flow_idx);
             BUILD_CUDA(cudaGetLastError());

@@ -33,6 +33,7 @@ struct wbpr_graph {
     int32_t s = 0, t = 0;     // as given (input ids)
     int32_t s_int = 0, t_int = 0;  // the solver's ids (differ when renumbered)
     bool renumbered = false;  // vertices renumbered by the builder (order != null)
+    bool lean = false;        // lean build: sort blocks that fit beside a resident server
     int32_t layout = 0;
     int64_t slots = 0;        // BCSR merged entries / RCSR arcs without loops
     int64_t mprime = 0;       // input arcs that are not self-loops

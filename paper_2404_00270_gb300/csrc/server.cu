@@ -82,6 +82,7 @@ void wbpr_server_default_options(wbpr_server_options *o)
     o->small_blocks = 88;    // 152 blocks = 1 per SM on a GB300: see wbpr.h
     o->idle_ms = 60000;
     o->big_slots = 1 << 15;
+    o->build_room = 1;
 }
 
 }  // extern "C"
@@ -92,8 +93,10 @@ namespace {
 // waits for the kernels already running -- the persistent server kernel,
 // which waits for requests whose builds would need that load: a deadlock
 // until the idle limit.  So before the server starts, every kernel a build
-// can launch is loaded: two throw-away builds of the server's layout, one
-// tiny and one past the single-tile sizes of the sort and scan routines.
+// can launch is loaded: throw-away builds of the server's layout, one tiny
+// and one past the single-tile sizes of the sort and scan routines, each
+// with a parallel arc (the duplicate-prefix kernels) and with both the lean
+// and the default builder tuning.
 wbpr_status preload_build_kernels(int layout)
 {
     static std::mutex mu;
@@ -101,20 +104,27 @@ wbpr_status preload_build_kernels(int layout)
     std::lock_guard<std::mutex> lock(mu);
     const int k = layout == WBPR_BCSR ? 1 : 0;
     if (done[k]) return WBPR_OK;
-    for (int64_t m : {(int64_t)3, (int64_t)1 << 17}) {
-        const int64_t n = m + 2;
-        std::vector<int32_t> src((size_t)m), dst((size_t)m), cap((size_t)m, 1);
-        for (int64_t i = 0; i < m; ++i) {
-            src[(size_t)i] = (int32_t)(i % n);
-            dst[(size_t)i] = (int32_t)((i * 7 + 1) % n);
+    for (int lean = 0; lean < 2; ++lean)
+        for (int64_t m : {(int64_t)3, (int64_t)1 << 17}) {
+            const int64_t n = m + 2;
+            std::vector<int32_t> src((size_t)m), dst((size_t)m), cap((size_t)m, 1);
+            for (int64_t i = 0; i < m; ++i) {
+                src[(size_t)i] = (int32_t)(i % n);
+                dst[(size_t)i] = (int32_t)((i * 7 + 1) % n);
+            }
+            src[(size_t)m - 1] = src[0];  // a parallel arc
+            dst[(size_t)m - 1] = dst[0];
+            wbpr_options o;
+            wbpr_default_options(&o);
+            o.lean_build = lean;
+            wbpr_graph *g = wbpr_build_ex(n, m, src.data(), dst.data(), cap.data(), 0, 1, (wbpr_layout)layout, &o,
+                                          nullptr);
+            if (!g) return wbpr_last_error();
+            int64_t v = 0;
+            wbpr_status rc = wbpr_maxflow(g, nullptr, &v, nullptr);
+            wbpr_destroy(g);
+            if (rc != WBPR_OK) return rc;
         }
-        wbpr_graph *g = wbpr_build(n, m, src.data(), dst.data(), cap.data(), 0, 1, (wbpr_layout)layout);
-        if (!g) return wbpr_last_error();
-        int64_t v = 0;
-        wbpr_status rc = wbpr_maxflow(g, nullptr, &v, nullptr);
-        wbpr_destroy(g);
-        if (rc != WBPR_OK) return rc;
-    }
     done[k] = true;
     return WBPR_OK;
 }
@@ -123,7 +133,8 @@ wbpr_server *server_start_impl(const wbpr_server_options &o)
 {
     if ((o.layout != WBPR_BCSR && o.layout != WBPR_RCSR) || o.capacity < 1 || o.team_blocks < 1 ||
         o.team_blocks > 64 || (o.team_blocks & (o.team_blocks - 1)) || o.big_teams < 0 || o.small_blocks < 0 ||
-        o.big_teams + o.small_blocks < 1 || o.idle_ms < 1 || o.big_slots < 0) {
+        o.big_teams + o.small_blocks < 1 || o.idle_ms < 1 || o.big_slots < 0 || o.build_room < 0 ||
+        o.build_room > 1) {
         set_error(WBPR_EINVAL, "wbpr_server_start: invalid options");
         return nullptr;
     }
@@ -140,7 +151,7 @@ wbpr_server *server_start_impl(const wbpr_server_options &o)
     const int layout = o.layout == WBPR_BCSR ? kBCSR : kRCSR;
     int per_sm = 0, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    if (server_max_blocks_per_sm(layout, &per_sm) != cudaSuccess) {
+    if (server_max_blocks_per_sm(layout, &per_sm, o.build_room != 0) != cudaSuccess) {
         cudaGetLastError();
         free_server(s);
         set_error(WBPR_ECUDA, "wbpr_server_start: occupancy query failed");
@@ -200,7 +211,7 @@ wbpr_server *server_start_impl(const wbpr_server_options &o)
         return nullptr;
     }
     cudaError_t e = cudaMemsetAsync(s->d_ctl, 0, s->d_ctl_bytes, s->stream);
-    if (e == cudaSuccess) e = server_launch(layout, (int)grid, d, s->stream);
+    if (e == cudaSuccess) e = server_launch(layout, (int)grid, d, s->stream, o.build_room != 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_server(s);
@@ -390,7 +401,7 @@ wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream
         std::stable_sort(small.begin(), small.end(), by_size);
         const int layout = lay ? kBCSR : kRCSR;
         int per_sm = 0;
-        if (server_max_blocks_per_sm(layout, &per_sm) != cudaSuccess || per_sm < 1) {
+        if (server_max_blocks_per_sm(layout, &per_sm, false) != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             return set_error(WBPR_ECUDA, "wbpr_maxflow_batch: occupancy query failed");
         }
@@ -427,6 +438,7 @@ wbpr_status wbpr_maxflow_batch(wbpr_graph *const *gs, int32_t count, wbpr_stream
         o.small_blocks = (int32_t)small_blocks;
         o.big_slots = bo.batch_big_slots;
         o.idle_ms = bo.barrier_timeout_ms;
+        o.build_room = 0;  // nothing is built while the batch's server runs
         wbpr_server *srv = server_start_impl(o);
         if (!srv) return wbpr_last_error();
         std::vector<std::pair<int, int64_t>> tickets;

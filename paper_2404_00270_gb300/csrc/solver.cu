@@ -54,16 +54,36 @@ static void *pick_server_kernel(int layout)
     return layout == kBCSR ? server_kernel_bcsr() : server_kernel_rcsr();
 }
 
-cudaError_t server_max_blocks_per_sm(int layout, int *blocks)
+// An SM's split between L1 and shared memory is fixed while any block runs
+// on it.  A server that admits builds while it is resident (build_room)
+// asks for the largest shared-memory carveout, so that the builds' blocks
+// (sort and scan tiles of up to 34 KB in a lean build) find shared memory
+// beside its blocks; with the default carveout the split chosen for the
+// server's own blocks left too little, and builds waited for the server to
+// exit.  A batch, which builds nothing while its server runs, keeps the
+// default (more L1).
+static cudaError_t server_carveout(void *k, bool build_room)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pick_server_kernel(layout), kBlock, 0);
+    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                build_room ? (int)cudaSharedmemCarveoutMaxShared : (int)cudaSharedmemCarveoutDefault);
 }
 
-cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream)
+cudaError_t server_max_blocks_per_sm(int layout, int *blocks, bool build_room)
+{
+    void *k = pick_server_kernel(layout);
+    cudaError_t e = server_carveout(k, build_room);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kBlock, 0);
+}
+
+cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream, bool build_room)
 {
     ServerDesc local = d;
     void *args[] = {&local};
-    return cudaLaunchCooperativeKernel(pick_server_kernel(layout), dim3(grid), dim3(kBlock), args, 0, stream);
+    void *k = pick_server_kernel(layout);
+    cudaError_t e = server_carveout(k, build_room);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kBlock), args, 0, stream);
 }
 
 static void *pick_kernel(int layout, int small_tile)

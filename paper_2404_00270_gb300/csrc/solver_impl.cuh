@@ -2082,14 +2082,18 @@ __device__ bool cut_capacity(Ctx &c, long long &sum)
 
 // Direction of the next BFS level (after Beamer, Asanovic and Patterson):
 // bottom-up when the frontier holds at least bottom_up_min vertices and,
-// with bottom_up_edges, its residual-list entries times bottom_up reach the
-// entries of the vertices not yet visited (nor written off); otherwise its
-// vertex count times bottom_up must reach the unvisited vertices.
+// by the entry rule, its residual-list entries times bottom_up reach the
+// entries of the vertices not yet visited (nor written off); by the vertex
+// rule, its vertex count times bottom_up must reach the unvisited vertices.
+// bottom_up_edges: 0 = vertex rule, 1 = entry rule, 2 = entry rule where
+// `entry_ok` (the searches of phase 1 and of the cut), vertex rule in the
+// searches of phase 2, where many unvisited vertices never find a parent and
+// a bottom-up level scans their whole rows.
 __device__ __forceinline__ bool bottom_up_level(const Params &P, unsigned tot, long long fe, long long unseen_edges,
-                                                long long unseen)
+                                                long long unseen, bool entry_ok)
 {
     if (P.bottom_up <= 0 || tot < (unsigned)P.bottom_up_min) return false;
-    if (P.bottom_up_edges) return fe * P.bottom_up >= unseen_edges;
+    if (P.bottom_up_edges == 1 || (P.bottom_up_edges == 2 && entry_ok)) return fe * P.bottom_up >= unseen_edges;
     return (long long)tot * P.bottom_up >= unseen;
 }
 
@@ -2165,7 +2169,7 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         seen += tot;
         const long long fe = __ldcg(&P.st.ctl->fedges[c.gen % 3]);
         unseen_edges -= fe;
-        const bool bu_mode = bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen);
+        const bool bu_mode = bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen, phase1);
         if (bu_mode)
             bfs_level_bu<L, kBfsBackward>(c, base + level + 1);
         else
@@ -2430,7 +2434,7 @@ __device__ bool min_cut(Ctx &c)
         seen += tot;
         const long long fe = __ldcg(&P.st.ctl->fedges[c.gen % 3]);
         unseen_edges -= fe;
-        const bool bu_mode = bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen);
+        const bool bu_mode = bottom_up_level(P, tot, fe, unseen_edges, (long long)n - seen, true);
         if (bu_mode)
             bfs_level_bu<L, kBfsForward>(c, level + 2);
         else

@@ -203,8 +203,8 @@ struct ServerDesc {
     unsigned long long idle_ns;
     unsigned long long timeout_ns;
 };
-cudaError_t server_max_blocks_per_sm(int layout, int *blocks);
-cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream);
+cudaError_t server_max_blocks_per_sm(int layout, int *blocks, bool build_room);
+cudaError_t server_launch(int layout, int grid, const ServerDesc &d, cudaStream_t stream, bool build_room);
 
 // Launch helpers implemented in solver.cu.
 cudaError_t solver_max_blocks_per_sm(int layout, int small_tile, int *blocks, size_t dyn_smem = 0);

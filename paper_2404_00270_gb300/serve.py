@@ -20,7 +20,7 @@ import time
 import torch
 
 from . import (WBPR_BCSR, load, torch_allocator_enabled, use_torch_allocator, wbpr_build,
-               wbpr_get_info, wbpr_server_default_options,
+               wbpr_default_options, wbpr_get_info, wbpr_server_default_options,
                wbpr_server_poll, wbpr_server_start, wbpr_server_stop, wbpr_server_submit,
                wbpr_server_team_exits, wbpr_server_times)
 
@@ -79,11 +79,11 @@ class Server:
         self.opts = wbpr_server_default_options()
         self.opts.layout = layout
         self.opts.big_slots = big_slots
-        # one server block per SM: the rest of every SM stays free for the
-        # builds that admission runs while the server kernel is resident (a
-        # build's radix-sort block needs more registers than two server blocks
-        # leave on an SM)
-        total = torch.cuda.get_device_properties(self.device).multi_processor_count
+        # two server blocks per SM: the rest of every SM stays free for the
+        # builds that admission runs while the server kernel is resident; they
+        # are lean builds (wbpr_options.lean_build), whose largest blocks fit
+        # in the registers two server blocks leave on an SM
+        total = 2 * torch.cuda.get_device_properties(self.device).multi_processor_count
         if big_teams is None:
             big_teams = max(1, (total * 3 // 5) // team_blocks)
         if small_blocks is None:
@@ -92,6 +92,8 @@ class Server:
         self.opts.big_teams = big_teams
         self.opts.small_blocks = small_blocks
         self.opts.idle_ms = idle_ms
+        self.build_opts = wbpr_default_options()
+        self.build_opts.lean_build = 1
         self.in_use = 0
         self.peak_in_use = 0
         self.stall_s = 120.0
@@ -136,7 +138,7 @@ class Server:
                         continue
                     tb = time.perf_counter()
                     g = wbpr_build(req.n, req.m, req.src, req.dst, req.cap, req.s, req.t, self.layout,
-                                   None, build_stream)
+                                   self.build_opts, build_stream)
                     req.build_ms = 1e3 * (time.perf_counter() - tb)
                     if self.table is not None:
                         from .autotune import apply_table

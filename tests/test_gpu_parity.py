@@ -158,15 +158,22 @@ def test_single_push_mode_small_graphs(layout):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
-def test_builder_arrays_bit_exact(layout):
+@pytest.mark.parametrize("lean", [0, 1])
+def test_builder_arrays_bit_exact(layout, lean):
+    """Every builder array equals the by-definition layout, with duplicate,
+    antiparallel and self-loop arcs, for CUB's tuning and for lean builds
+    (256-thread sort blocks, duplicate prefixes by run), on inputs past and
+    within the single-tile size of the sorts."""
     m = wb()
-    for seed in range(4):
-        inst = W.random_small(200 + 50 * seed, 3000, 300 + seed, cap_lo=0, cap_hi=1000)
+    o = m.wbpr_default_options()
+    o.lean_build = lean
+    for seed in range(5):
+        inst = W.random_small(200 + 50 * seed, 3000 if seed < 4 else 400, 300 + seed, cap_lo=0, cap_hi=1000)
         src, dst, cap = inst.numpy()
         src = np.concatenate([src, src[:100], dst[100:300], [5, 9]])
         dst = np.concatenate([dst, dst[:100], src[100:300], [5, 9]])
         cap = np.concatenate([cap, cap[:100], cap[100:300], [3, 4]])
-        G = m.wbpr_build(inst.n, src.size, src, dst, cap, inst.s, inst.t, layout_code(layout))
+        G = m.wbpr_build(inst.n, src.size, src, dst, cap, inst.s, inst.t, layout_code(layout), o)
         ref = layouts.bcsr(inst.n, src, dst, cap) if layout == "bcsr" else layouts.rcsr(inst.n, src, dst, cap)
         for key, val in ref.items():
             got = m.wbpr_export(G, key)
