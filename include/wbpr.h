@@ -138,9 +138,10 @@ typedef struct wbpr_options {
     int32_t bottom_up_edges;  /* BFS direction rule: 1 = compare the residual-list
                                  entries of the frontier, times bottom_up, with
                                  those of the vertices not yet visited; 0 = compare
-                                 vertex counts (default); 2 = entries in the global
-                                 relabels of phase 1 and in the cut, vertex counts
-                                 in the global relabels of phase 2 */
+                                 vertex counts; 2 = entries in the global relabels
+                                 of phase 1 and in the cut, vertex counts in the
+                                 global relabels of phase 2; -1 = automatic (default):
+                                 2 from 2^21 vertices, else 0 */
     int32_t avq_incremental;  /* 1 = between two global relabels, build the AVQ only
                                  from the vertices the last pass pushed into or left
                                  with excess (a bitmap the pushes mark); the first

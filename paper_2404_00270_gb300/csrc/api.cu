@@ -120,7 +120,7 @@ void wbpr_default_options(wbpr_options *o)
     o->warp_time = 0;
     o->stage_hubs = 0;
     o->barrier_extra = 0;
-    o->bottom_up_edges = 0;
+    o->bottom_up_edges = -1;
     o->avq_incremental = 2;
 }
 
@@ -171,7 +171,7 @@ static wbpr_status check_options(const wbpr_options *o)
     if (o->warp_time != 0 && o->warp_time != 1) return WBPR_EINVAL;
     if (o->barrier_extra < 0 || o->barrier_extra > 1024) return WBPR_EINVAL;
     if (o->stage_hubs != 0 && o->stage_hubs != 1) return WBPR_EINVAL;
-    if (o->bottom_up_edges < 0 || o->bottom_up_edges > 2) return WBPR_EINVAL;
+    if (o->bottom_up_edges < -1 || o->bottom_up_edges > 2) return WBPR_EINVAL;
     if (o->avq_incremental < 0 || o->avq_incremental > 2) return WBPR_EINVAL;
     if (o->lean_build != 0 && o->lean_build != 1) return WBPR_EINVAL;
     return WBPR_OK;
@@ -474,7 +474,9 @@ Params make_params(wbpr_graph *g, int mode)
     p.warp_max = g->opts.warp_max_degree;
     p.bottom_up = g->opts.bottom_up;
     p.bottom_up_min = g->opts.bottom_up_min;
-    p.bottom_up_edges = g->opts.bottom_up_edges;
+    // automatic: the entry rule in phase 1 and the cut from 2^21 vertices (heights
+    // beyond L2, long BFS levels over hub rows), the vertex rule below
+    p.bottom_up_edges = g->opts.bottom_up_edges >= 0 ? g->opts.bottom_up_edges : (g->n >= (1LL << 21) ? 2 : 0);
     p.max_iterations = g->opts.max_iterations;
     p.timeout_ns = (unsigned long long)g->opts.barrier_timeout_ms * 1000000ull;
     if (g->opts.trace > 0) {

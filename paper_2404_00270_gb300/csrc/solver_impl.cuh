@@ -102,8 +102,6 @@ struct Smem {
     long long bcast64;
     int bcast32;
     long long stats[kStatCount];
-    unsigned item;
-    unsigned hub_pos, hub_j, hub_nch;
     int ok;
 };
 
@@ -287,17 +285,17 @@ __device__ __forceinline__ void reset_local_slot(Ctx &c, int gen)
 
 // ---------------------------------------------------------------------------
 // Hub class: a vertex whose residual list is longer than warp_max is split
-// into chunks: of kWChunk entries for a push-relabel pass (one warp each),
-// of kChunk entries for a BFS level or the cut (one block each).  One 64-bit
-// atomic gives it both its queue position and the id of its first chunk; the
-// appender then records the position under each of its chunk ids, so a warp
-// or block that takes a chunk id finds its hub with one load.  A push-relabel
-// hub's chunks start `lead` = off[u] mod 4 slots before its row (BCSR), so
-// that chunk boundaries fall on 16-byte boundaries of the slot arrays.
+// into chunks of kWChunk entries (push-relabel passes, BFS levels and the
+// cut), each taken by one warp.  One 64-bit atomic gives it both its queue
+// position and the id of its first chunk; the appender then records the
+// position under each of its chunk ids, so a warp that takes a chunk id
+// finds its hub with one load.  A hub's chunks start `lead` = off[u] mod 4
+// slots before its row (BCSR), so that chunk boundaries fall on 16-byte
+// boundaries of the slot arrays.
 // ---------------------------------------------------------------------------
 constexpr u64 kChunkMask = (1ull << 40) - 1;
 
-__device__ __forceinline__ unsigned hub_chunks(long long deg, int chunk = kChunk, int lead = 0)
+__device__ __forceinline__ unsigned hub_chunks(long long deg, int chunk = kWChunk, int lead = 0)
 {
     return deg <= 0 ? 1u : (unsigned)((deg + lead + chunk - 1) / chunk);
 }
@@ -306,7 +304,7 @@ __device__ __forceinline__ unsigned hub_chunks(long long deg, int chunk = kChunk
 // chunk count in *first / *nch.  With fill = false the caller writes the
 // chunk table (warp_fill_chunks).
 __device__ __forceinline__ unsigned hub_append(Ctx &c, int slot3, int set, int v, long long deg, bool pr,
-                                               long long ev, int chunk = kChunk, int lead = 0,
+                                               long long ev, int chunk = kWChunk, int lead = 0,
                                                bool fill = true, unsigned *first_out = nullptr,
                                                unsigned *nch_out = nullptr)
 {
@@ -389,32 +387,6 @@ __device__ __forceinline__ unsigned queue_total(const Ctl *ctl, int gen)
     const int s3 = gen % 3;
     return __ldcg(&ctl->q_count[s3][0]) + __ldcg(&ctl->q_count[s3][1]) +
            (unsigned)(__ldcg(&ctl->hub_pack[s3]) >> 40);
-}
-
-// Take the next hub chunk of generation (s3, set).  Block-uniform result.
-__device__ bool grab_chunk(Ctx &c, int s3, int set, unsigned nh, unsigned nchunks, unsigned &pos,
-                           unsigned &j, unsigned &nch)
-{
-    if (threadIdx.x == 0) {
-        const unsigned id = atomicAdd(&c.P.st.ctl->q_grab[s3], 1u);
-        if (id < nchunks) {
-            const unsigned *start = c.P.st.hub_start[set];
-            const unsigned lo = __ldcg(c.P.st.hub_chunk[set] + id);  // start[lo] <= id < start[lo + 1]
-            const unsigned s0 = __ldcg(start + lo);
-            const unsigned s1 = lo + 1 < nh ? __ldcg(start + lo + 1) : nchunks;
-            c.sm.hub_pos = lo;
-            c.sm.hub_j = id - s0;
-            c.sm.hub_nch = s1 - s0;
-        }
-        c.sm.item = id;
-    }
-    __syncthreads();
-    const bool ok = c.sm.item < nchunks;
-    pos = c.sm.hub_pos;
-    j = c.sm.hub_j;
-    nch = c.sm.hub_nch;
-    __syncthreads();
-    return ok;
 }
 
 // Row index r of u's residual list -> slot (RCSR: out entries, then in entries).
@@ -1758,7 +1730,8 @@ __device__ void bfs_level(Ctx &c, int val)
 // entries read differ.  Only v's owner writes v's level, so no claim is
 // needed.  Rows of up to kBuThread entries are
 // scanned by one thread (kBuVerts vertices per thread, 4 entries per step),
-// longer rows by a warp, hub rows by the whole block.
+// longer rows by a warp, hub rows by a warp for their first kBuHubHead
+// entries and by the whole block for the rest.
 // ---------------------------------------------------------------------------
 constexpr int kBuThread = 32;
 constexpr int kBuStep = 4;
@@ -1975,9 +1948,10 @@ __device__ void bfs_level_bu(Ctx &c, int val)
 // initial capacities; this thread's share (valid once it returns true).
 // Rows of up to kBuThread entries are summed by one thread (kBuVerts vertices
 // at once).  Longer rows are queued in the next (empty) queue generation and,
-// after a barrier, taken across the grid: a warp per row, hub rows by chunks
-// of whole blocks.  R-MAT places its long rows at low ids, so rows handled by
-// the block that found them would all land on a few blocks.
+// after a barrier, taken across the grid: a warp per row, hub rows in
+// kWChunk-entry chunks taken by warps.  R-MAT places its long rows at low
+// ids, so rows handled by the block that found them would all land on a few
+// blocks.
 template <int L>
 __device__ bool cut_capacity(Ctx &c, long long &sum)
 {
@@ -2006,7 +1980,8 @@ __device__ bool cut_capacity(Ctx &c, long long &sum)
                 deg[i] = __ldg(g.off + v + 1) - ob[i];
                 if (deg[i] > kBuThread) {
                     live[i] = false;
-                    if (classify(P, deg[i]) == 2) hub_append(c, n3, nset, (int)v, deg[i], false, 0);
+                    if (classify(P, deg[i]) == 2)
+                        hub_append(c, n3, nset, (int)v, deg[i], false, 0, kWChunk, hub_lead<L>(g, (int)v));
                     else q_append(c, n3, nset, 1, (int)v);
                 }
             }
@@ -2056,21 +2031,24 @@ __device__ bool cut_capacity(Ctx &c, long long &sum)
         }
     }
 
+    // hub rows: chunks of kWChunk entries (starting on a 16-byte boundary in
+    // BCSR, as in a push-relabel pass) taken by warps, the hub's row bounds
+    // kept across a warp's consecutive chunks
     const u64 hp = __ldcg(&P.st.ctl->hub_pack[n3]);
     const unsigned nh = (unsigned)(hp >> 40), nchunks = (unsigned)(hp & kChunkMask);
     unsigned pos, j, nch;
     if (nchunks) {
-        while (grab_chunk(c, n3, nset, nh, nchunks, pos, j, nch)) {
-            const int u = __ldcg(P.st.q[nset][2] + pos);
-            const long long b = __ldg(g.off + u), e = __ldg(g.off + u + 1);
-            const long long r0 = b + (long long)j * kChunk, r1 = e < r0 + kChunk ? e : r0 + kChunk;
-            constexpr int NB = kChunk / kBlock;
+        WGrab gb(nchunks, c.nblk * kWarps);
+        while (grab_wchunk<L>(c, n3, nset, nh, nchunks, gb, pos, j, nch)) {
+            const long long lo = (long long)j * kWChunk - (L == kBCSR ? (gb.ob & 3) : 0);
+            constexpr int NB = kWChunk / 32;
             int w[NB], cap[NB];
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
-                const long long k = r0 + (long long)q * kBlock + threadIdx.x;
-                w[q] = k < r1 ? __ldg(g.col + k) : 0;
-                cap[q] = k < r1 ? __ldg(g.cf0 + k) : 0;
+                const long long r = lo + lane + 32LL * q;
+                const bool ok = r >= 0 && r < gb.dout;
+                w[q] = ok ? __ldg(g.col + gb.ob + r) : 0;
+                cap[q] = ok ? __ldg(g.cf0 + gb.ob + r) : 0;
             }
 #pragma unroll
             for (int q = 0; q < NB; ++q)

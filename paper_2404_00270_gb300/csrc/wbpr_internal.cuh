@@ -28,13 +28,12 @@ constexpr int kClasses = 3;         // tile classes: small tile, warp, block
 constexpr int kQueueCap = 1024;     // per-class shared-memory staging of queue appends
 constexpr int kUnvisited = 0x7fffffff;
 constexpr long long kRenumberAutoVertices = 1LL << 22;  // renumber = -1: on from this many vertices
-constexpr int kChunk = 2048;        // hub rows of a BFS level or of the cut are processed in chunks
-                                    // of this many entries, one chunk per block, taken dynamically
 #ifndef WBPR_WCHUNK
 #define WBPR_WCHUNK 256
 #endif
-constexpr int kWChunk = WBPR_WCHUNK;  // hub rows of a push-relabel pass: chunks of this many entries,
-                                      // one chunk per warp (kWChunk / 32 per lane), taken dynamically
+constexpr int kWChunk = WBPR_WCHUNK;  // hub rows (push-relabel passes, BFS levels, the cut): chunks of
+                                      // this many entries, one per warp (kWChunk / 32 per lane), taken
+                                      // dynamically
 // Staging of push-relabel hub chunks in shared memory: per warp two buffers
 // of kWChunk entries (neighbour ids and residual capacities).
 constexpr int kStageInts = 2 * 2 * WBPR_WCHUNK;            // per warp

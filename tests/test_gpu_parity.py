@@ -183,7 +183,7 @@ def test_builder_arrays_bit_exact(layout, lean):
 
 # (bottom_up, bottom_up_min, bottom_up_edges)
 BU_MODES = {"top-down": (0, 1024, 1), "default": (14, 1024, 1), "vertex-rule": (14, 1024, 0),
-            "bottom-up": (1 << 20, 1, 0)}
+            "phase-aware": (14, 1024, 2), "bottom-up": (1 << 20, 1, 0)}
 
 
 def _bu_options(m, mode):
