@@ -189,7 +189,7 @@ extern "C" wbpr_status wbpr_maxflow_bcsr_noalloc(int32_t n, int64_t slots, int32
     p.warp_max = o.warp_max_degree;
     p.bottom_up = o.bottom_up;
     p.bottom_up_min = o.bottom_up_min;
-    p.bottom_up_edges = o.bottom_up_edges;
+    p.bottom_up_edges = 0;                   // the automatic rule's choice below 2^21 vertices
     p.max_iterations = o.max_iterations;
     p.timeout_ns = (unsigned long long)o.barrier_timeout_ms * 1000000ull;
 

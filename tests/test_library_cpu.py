@@ -50,9 +50,20 @@ def test_argument_errors_without_gpu(wb):
     assert e.value.status == -1
     o = wb.wbpr_default_options()
     assert o.use_rev == 1 and o.gap == 1 and o.small_tile == 8
+    assert o.avq_incremental == 2 and o.lean_build == 0 and o.bottom_up_edges == -1
     o.small_tile = 5
     with pytest.raises(wb.WbprError):
         wb.wbpr_build(4, 1, [0], [1], [1], 0, 1, opts=o)
+    # the option ranges are checked before anything touches a device
+    for field, bad in [("avq_incremental", 3), ("avq_incremental", -1), ("lean_build", 2),
+                       ("bottom_up_edges", 3), ("bottom_up_edges", -2)]:
+        o = wb.wbpr_default_options()
+        setattr(o, field, bad)
+        with pytest.raises(wb.WbprError) as e:
+            wb.wbpr_build(4, 1, [0], [1], [1], 0, 1, opts=o)
+        assert e.value.status == -1, field
+    so = wb.wbpr_server_default_options()
+    assert so.build_room == 1
     assert wb.wbpr_error_string(-4).startswith("iteration cap")
 
 
