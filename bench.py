@@ -226,6 +226,50 @@ def cpu_sample(scale: int = 20, seed: int = 2, cap_hi: int = 1000):
             "time_to_solution_s": secs, "flow_value": r["value"]}
 
 
+def _oracle_worker_init():
+    import oracle  # noqa: F401  (loaded once per worker, before the timed region)
+
+
+def _oracle_value(inst):
+    """The oracle's value (no flow, no cut) of one instance given as
+    (n, src, dst, cap, s, t); a task of batch_cpu_baseline's pool."""
+    import oracle
+    n, src, dst, cap, s, t = inst
+    return oracle.maxflow_pr(n, src, dst, cap, s, t, want_flow=False, want_cut=False)["value"]
+
+
+def batch_cpu_baseline(specs, sample: int) -> dict:
+    """The oracle, as it stands, on an evenly spaced sample of the batch mix:
+    solves/s on one host core, and with one worker process per host core
+    (spawned, so that the pool is safe beside a CUDA context)."""
+    import multiprocessing as mp
+    import oracle
+    import workloads as W
+    oracle.build()
+    stride = max(1, len(specs) // sample)
+    picked = [list(specs[i]) for i in range(0, len(specs), stride)][:sample]
+    insts = []
+    for sp in picked:
+        g = W.make_from_spec(tuple(sp))
+        insts.append((g.n, *g.numpy(), g.s, g.t))
+    t0 = time.perf_counter()
+    for inst in insts:
+        _oracle_value(inst)
+    one = len(insts) / (time.perf_counter() - t0)
+    cores = max(1, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init) as pool:
+        pool.map(_oracle_value, insts[:1] * cores, chunksize=1)  # every worker started
+        t0 = time.perf_counter()
+        pool.map(_oracle_value, insts, chunksize=1)
+        allc = len(insts) / (time.perf_counter() - t0)
+    return {"value": one, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(picked)} evenly spaced instances of the {len(specs):,}-instance mix (every "
+                      f"{stride}th), drawn on the host; FIFO push-relabel, value only; one thread",
+            "all_cores": {"value": allc, "unit": "solves/s", "cores": cores,
+                          "sample": "the same instances, one worker process per host core (the largest "
+                                    "instance bounds the time)"}}
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -587,6 +631,10 @@ def run_batch(args):
     res = batch_measure(args.batch_count, args.steps, args.warmup, args.plain_sample, args.serve_count,
                         args.serve_rates, tune=args.tune)
     clocks = sampler.stop()
+    cpu = None
+    if args.oracle_sample > 0:
+        import workloads as W
+        cpu = batch_cpu_baseline(W.batch_spec(args.batch_count), args.oracle_sample)
     line = {
         "metric": f"batched solves/s ({res['instances']:,}-instance mix, one batched launch)",
         "value": res["batched_solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
@@ -595,6 +643,8 @@ def run_batch(args):
         "config": dict(res, workload=f"batch-mix-{res['instances']}"),
         "roofline": None, "clocks": clocks, "gpu_launches": args.steps * 2,
     }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line))
 
 
@@ -686,6 +736,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=512)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0])
     ap.add_argument("--tune", action="store_true", help="batch: per-class tuned knobs, timed again")
+    ap.add_argument("--oracle-sample", type=int, default=32,
+                    help="batch: instances of the mix the CPU oracle solves for cpu_baseline (0 = none)")
     ap.add_argument("--options", default="",
                     help='library options of the timed handle as JSON, e.g. {"thread_centric": 1} (profiling)')
     args = ap.parse_args()
