@@ -2120,10 +2120,33 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         }
     }
     const long long stride = (long long)c.nblk * kBlock;
-    for (long long v = c.bid * kBlock + threadIdx.x; v <= n; v += stride) {
+    // Four vertices per thread and step (16-byte height and count stores,
+    // 4-byte reads of the marks), the last n mod 4 and count[n] one by one.
+    const long long n4 = (long long)n & ~3LL;
+    for (long long q = c.bid * kBlock + threadIdx.x; 4 * q < n4; q += stride) {
+        const long long v0 = 4 * q;
+        if (gap) __stcg(reinterpret_cast<int4 *>(P.st.count) + q, make_int4(0, 0, 0, 0));
+        uchar4 d4 = make_uchar4(0, 0, 0, 0);
+        if (first_of_phase2) reinterpret_cast<uchar4 *>(P.st.dead)[q] = d4;  // phase 1's marks mean "cannot reach t"
+        else d4 = reinterpret_cast<const uchar4 *>(P.st.dead)[q];
+        const unsigned char d[4] = {d4.x, d4.y, d4.z, d4.w};
+        bool all = true;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) all = all && !d[i] && v0 + i != excluded;
+        if (all) {
+            int4 hv = make_int4(kUnvisited, kUnvisited, kUnvisited, kUnvisited);
+            if (target >= v0 && target < v0 + 4) (&hv.x)[target - v0] = base;
+            __stcg(reinterpret_cast<int4 *>(P.st.h) + q, hv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (!d[i] && v0 + i != excluded) __stcg(P.st.h + v0 + i, v0 + i == target ? base : kUnvisited);
+        }
+    }
+    for (long long v = n4 + c.bid * kBlock + threadIdx.x; v <= n; v += stride) {
         if (gap) __stcg(P.st.count + v, 0);
         if (v == n || v == excluded) continue;
-        if (first_of_phase2) P.st.dead[v] = 0;  // phase 1's marks mean "cannot reach t"
+        if (first_of_phase2) P.st.dead[v] = 0;
         else if (P.st.dead[v]) continue;
         __stcg(P.st.h + v, v == target ? base : kUnvisited);
     }
@@ -2156,18 +2179,27 @@ __device__ bool global_relabel(Ctx &c, bool phase1, bool first_of_phase2 = false
         c.gen++;
     }
     long long wo = 0, nd = 0, nde = 0;
-    for (long long v = c.bid * kBlock + threadIdx.x; v < n; v += stride) {
-        if (v == excluded) continue;
-        if (__ldcg(P.st.h + v) == kUnvisited) {
-            __stcg(P.st.h + v, unreach);
-            if (!P.st.dead[v]) {
-                P.st.dead[v] = 1;
-                ++nd;
-                nde += degree<L>(g, (int)v);
-                if (phase1) wo += __ldcg(P.st.e + v);
-            }
+    // Unreached vertices: the height cap, a mark, and (phase 1) the write-off.
+    // Four heights per thread and step (one 16-byte read), the last n mod 4
+    // one by one.
+    auto finish = [&](long long v) {
+        __stcg(P.st.h + v, unreach);
+        if (!P.st.dead[v]) {
+            P.st.dead[v] = 1;
+            ++nd;
+            nde += degree<L>(g, (int)v);
+            if (phase1) wo += __ldcg(P.st.e + v);
         }
+    };
+    for (long long q = c.bid * kBlock + threadIdx.x; 4 * q < n4; q += stride) {
+        const int4 hv = __ldcg(reinterpret_cast<const int4 *>(P.st.h) + q);
+        const int h4[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (h4[i] == kUnvisited && 4 * q + i != excluded) finish(4 * q + i);
     }
+    for (long long v = n4 + c.bid * kBlock + threadIdx.x; v < n; v += stride)
+        if (v != excluded && __ldcg(P.st.h + v) == kUnvisited) finish(v);
     long long bw = block_sum(c, wo);
     if (threadIdx.x == 0 && bw) {
         atomicAdd((u64 *)&P.st.ctl->excess_total, (u64)(-bw));
