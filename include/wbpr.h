@@ -379,9 +379,9 @@ wbpr_status wbpr_export(const wbpr_graph *g, int32_t what, void *host_dst, int64
  * every slot with one in its neighbour's row that points back.  Arrays that
  * fail return WBPR_EINVAL and nothing is solved.  The call synchronises
  * `stream` (twice: after the check and after the solve) and returns the
- * solve's status.  The first call on a
- * device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture.  Every
+ * solve's status; because it synchronises, no call of it can be recorded
+ * into a CUDA graph by stream capture.  The first call on a device looks up
+ * the array's device address (once per device, with that device current).  Every
  * call shares the one array, which keeps the last call's contents (the call
  * clears what must start at zero), so calls that overlap on the GPU -- from
  * two host threads or two streams -- race and must not be issued.
