@@ -19,6 +19,42 @@ def test_residual_distances(oracle_mod):
     P.pin_residual_dist()
 
 
+def test_residual_distances_match_library_shortest_paths(oracle_mod):
+    """The global-relabel heights of a residual snapshot (Section 2.2: the
+    exact distance to the sink over arcs with positive residual capacity,
+    never through the source) against SciPy's unweighted shortest paths on
+    the reversed graph with the source's arcs removed: an independent
+    breadth-first search on random arc lists with loops, duplicates and zero
+    residuals."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    import scipy.sparse as sp
+    import oracle
+    rng = np.random.default_rng(11)
+    for trial in range(60):
+        n = int(rng.integers(2, 200))
+        na = int(rng.integers(0, 6 * n))
+        tail = rng.integers(0, n, na).astype(np.int32)
+        head = rng.integers(0, n, na).astype(np.int32)
+        res = rng.integers(-1, 4, na).astype(np.int64)
+        target = int(rng.integers(0, n))
+        excluded = int(rng.integers(0, n)) if trial % 3 else -1
+        if excluded == target:
+            excluded = -1
+        base, unreach, excl_h = int(trial % 5), n + 7, n + 3
+        got = oracle.residual_dist(n, tail, head, res, target, excluded, base, unreach, excl_h)
+        keep = res > 0
+        if excluded >= 0:
+            keep &= (tail != excluded) & (head != excluded)
+        # reversed arcs head -> tail, so distances from the target are
+        # distances to it in the residual graph
+        a = sp.csr_matrix((np.ones(int(keep.sum())), (head[keep], tail[keep])), shape=(n, n))
+        d = csgraph.shortest_path(a, method="D", directed=True, unweighted=True, indices=target)
+        want = np.where(np.isfinite(d), base + np.nan_to_num(d, posinf=0).astype(np.int64), unreach)
+        if excluded >= 0:
+            want[excluded] = excl_h
+        assert got.tolist() == want.tolist(), (trial, n, na)
+
+
 def test_closed_forms(oracle_mod):
     P.pin_closed_forms()
 
