@@ -55,6 +55,11 @@ def test_residual_distances_match_library_shortest_paths(oracle_mod):
         assert got.tolist() == want.tolist(), (trial, n, na)
 
 
+def test_value_and_cut_side_match_scipy_maximum_flow(oracle_mod):
+    pytest.importorskip("scipy.sparse.csgraph")
+    P.pin_library_maxflow()
+
+
 def test_closed_forms(oracle_mod):
     P.pin_closed_forms()
 
