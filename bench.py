@@ -277,7 +277,10 @@ def run_reference(args):
     import oracle
     import workloads as W
     oracle.build()
-    g = W.rmat(18, 16, 2)
+    workload = args.workload if args.workload in WORKLOADS else "rmat26"
+    wl = WORKLOADS[workload]
+    # each step: the same R-MAT parameters (seed, capacities) at scale 18
+    g = W.rmat(18, 16, wl["seed"], cap_lo=1, cap_hi=wl["cap_hi"])
     src, dst, cap = g.numpy()
     times, arcs = [], []
     for i in range(args.warmup + args.steps):
@@ -289,14 +292,17 @@ def run_reference(args):
             arcs.append(r["stats"]["arcs_scanned"])
     total = sum(times)
     value = sum(arcs) / total
-    sample = (f"R-MAT scale 18 (edge factor 16, seed 2, {g.m} arcs) per step, a bounded sample of the "
-              f"R-MAT workload family; oracle phase 1 + 2 + edge flows + cut, 1 thread")
-    workload = args.workload if args.workload in WORKLOADS else "rmat26"
+    sample = (f"R-MAT scale 18 (edge factor 16, seed {wl['seed']}, capacities U[1,{wl['cap_hi']}], "
+              f"{g.m} arcs) per step, a bounded sample of the R-MAT {wl['scale']} workload (same "
+              f"generator and parameters, smaller scale); oracle phase 1 + 2 + edge flows + cut, 1 thread")
+    # the same workload as the GPU arm's line; each step is the bounded sample above
+    config = {"workload": f"{workload}-maxflow-mincut", "scale": wl["scale"], "edge_factor": 16,
+              "seed": wl["seed"], "capacities": f"U[1,{wl['cap_hi']}]",
+              "parallelism": "replicas" if world > 1 else "single", "sample_per_step": sample}
     line = {"metric": metric_name(workload), "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"rmat18-sample-of-{workload}", "layout": "adjacency list (oracle)"},
+            "data": "synthetic", "impl": "reference", "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

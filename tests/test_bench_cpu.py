@@ -28,6 +28,8 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.metric_name("rmat26")
     assert d["unit"] == "arcs/s" and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["config"]["workload"] == "rmat26-maxflow-mincut" and d["config"]["scale"] == 26
+    assert "R-MAT scale 18" in d["config"]["sample_per_step"]
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"] == {"value": d["value"], "unit": "arcs/s", "h2d_bytes_per_step": 0,
