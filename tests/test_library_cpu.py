@@ -88,3 +88,72 @@ def test_layout_restatement_by_hand(oracle_mod):
     assert list(r["in_offsets"]) == [0, 0, 1, 3, 5]
     assert list(r["in_col"]) == [0, 0, 1, 1, 2]
     assert list(r["flow_idx"]) == [0, 1, 2, 3, 4]
+
+
+def test_layout_restatement_invariants(oracle_mod):
+    """The layouts of §3.2 checked from their definition with plain Python
+    loops and dictionaries (no sorting or searching shared with the numpy
+    restatement), on random graphs with self-loops, duplicates and
+    antiparallel pairs: BCSR rows hold every neighbour joined in either
+    direction, in increasing id, with the summed capacity of the arcs u -> v,
+    rev pairs (u, v) with (v, u) both ways, arc2slot finds each arc's slot;
+    RCSR out rows keep the arcs by (head, input position), in rows by (tail,
+    out slot), and flow_idx points back at the same arc."""
+    import random
+    from oracle import layouts
+    NONE = 0xFFFFFFFF
+    rnd = random.Random(3)
+    for trial in range(200):
+        n = rnd.randint(2, 30)
+        m = rnd.randint(0, 120)
+        src = [rnd.randrange(n) for _ in range(m)]
+        dst = [rnd.randrange(n) for _ in range(m)]
+        cap = [rnd.randint(0, 50) for _ in range(m)]
+        b = layouts.bcsr(n, src, dst, cap)
+        off, col, bc, rev, a2s = (list(map(int, b[k])) for k in ("offsets", "col", "cap", "rev", "arc2slot"))
+        total = {}
+        nbrs = [set() for _ in range(n)]
+        for u, v, c in zip(src, dst, cap):
+            if u != v:
+                total[(u, v)] = total.get((u, v), 0) + c
+                nbrs[u].add(v)
+                nbrs[v].add(u)
+        assert off[0] == 0 and off[n] == len(col) == len(bc) == len(rev)
+        row_of = {}
+        for u in range(n):
+            assert off[u] <= off[u + 1]
+            row = col[off[u]:off[u + 1]]
+            assert row == sorted(nbrs[u]) and len(set(row)) == len(row)
+            for k in range(off[u], off[u + 1]):
+                row_of[k] = u
+                assert bc[k] == total.get((u, col[k]), 0)
+        for k in range(len(col)):
+            assert row_of[rev[k]] == col[k] and col[rev[k]] == row_of[k] and rev[rev[k]] == k
+        for i, (u, v) in enumerate(zip(src, dst)):
+            if u == v:
+                assert a2s[i] == NONE
+            else:
+                assert row_of[a2s[i]] == u and col[a2s[i]] == v
+
+        r = layouts.rcsr(n, src, dst, cap)
+        off, col, rc, a2s = (list(map(int, r[k])) for k in ("offsets", "col", "cap", "arc2slot"))
+        ioff, icol, fidx = (list(map(int, r[k])) for k in ("in_offsets", "in_col", "flow_idx"))
+        slot = 0
+        out_slot = {}
+        for u in range(n):
+            arcs = sorted((dst[i], i) for i in range(m) if src[i] == u and dst[i] != u)
+            assert off[u] == slot and off[u + 1] == slot + len(arcs)
+            for v, i in arcs:
+                assert col[slot] == v and rc[slot] == cap[i] and a2s[i] == slot
+                out_slot[i] = slot
+                slot += 1
+        assert off[n] == len(col) == slot
+        assert all(a2s[i] == NONE for i in range(m) if src[i] == dst[i])
+        pos = 0
+        for v in range(n):
+            ins = sorted((src[i], out_slot[i]) for i in range(m) if dst[i] == v and src[i] != v)
+            assert ioff[v] == pos and ioff[v + 1] == pos + len(ins)
+            for u, k in ins:
+                assert icol[pos] == u and fidx[pos] == k and col[k] == v
+                pos += 1
+        assert ioff[n] == pos == len(icol)
