@@ -127,11 +127,11 @@ class Server:
                 while arrived and len(outstanding) < max_inflight:
                     req = arrived[0]
                     need = footprint_estimate(req.n, req.m)
-                    verdict = admission(need, self.in_use, self.budget, bool(outstanding))
-                    if verdict == "wait":
+                    decision = admission(need, self.in_use, self.budget, bool(outstanding))
+                    if decision == "wait":
                         break
                     arrived.popleft()
-                    if verdict == "reject":
+                    if decision == "reject":
                         req.rejected = (f"footprint {need} B exceeds the memory budget of {self.budget} B")
                         req.done = time.perf_counter() - t0
                         last_progress = time.perf_counter()
