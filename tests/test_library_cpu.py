@@ -157,3 +157,25 @@ def test_layout_restatement_invariants(oracle_mod):
                 assert icol[pos] == u and fidx[pos] == k and col[k] == v
                 pos += 1
         assert ioff[n] == pos == len(icol)
+
+
+def test_no_fallback_without_the_cuda_library():
+    """The package has no CPU path: without libwbpr.so every call raises,
+    and importing it (and its serving and tuning modules) loads nothing from
+    the oracle."""
+    import subprocess
+    import sys
+    code = (
+        "import sys\n"
+        "import paper_2404_00270_gb300 as wb, paper_2404_00270_gb300.autotune, paper_2404_00270_gb300.serve\n"
+        "from paper_2404_00270_gb300 import _build\n"
+        "assert not any(k == 'oracle' or k.startswith('oracle.') for k in sys.modules), 'oracle imported'\n"
+        "_build.LIB = '/nonexistent/libwbpr.so'\n"
+        "try:\n"
+        "    wb.wbpr_build(4, 1, [0], [1], [1], 0, 1)\n"
+        "except RuntimeError as e:\n"
+        "    assert 'not built' in str(e), e\n"
+        "    print('raised')\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                         cwd=ROOT)
+    assert out.returncode == 0 and out.stdout.strip() == "raised", out.stderr[-2000:]
